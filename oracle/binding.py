@@ -1,0 +1,307 @@
+"""ctypes binding of the FP64 CPU oracle (hj_oracle.c) plus a pure-Python
+brute-force game-tree solver used to pin it.
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by __graft_entry__.smoke() and by
+the cpu_baseline / reference legs of bench.py.  The CUDA product path never
+imports this module.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from typing import Dict, Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hj_oracle.c")
+_LIB = os.path.join(_HERE, "libhj_oracle.so")
+
+MAXD = 6
+MAXIN = 6
+_MODEL = {"drift": 0, "quad_z": 1, "quad_x4": 2}
+_CON = {"box": 0, "ball_out": 1}
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_long * MAXD),
+                ("lo", ctypes.c_double * MAXD), ("hi", ctypes.c_double * MAXD),
+                ("model", ctypes.c_int), ("params", ctypes.c_double * 8),
+                ("nd", ctypes.c_int), ("d_lo", ctypes.c_double * MAXIN),
+                ("d_hi", ctypes.c_double * MAXIN), ("con_kind", ctypes.c_int),
+                ("con_a", ctypes.c_double * MAXD), ("con_b", ctypes.c_double * MAXD)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("scheme", ctypes.c_int), ("cfl", ctypes.c_double), ("dt", ctypes.c_double),
+                ("tol", ctypes.c_double), ("check_dt", ctypes.c_double),
+                ("max_steps", ctypes.c_long), ("fixed_steps", ctypes.c_long),
+                ("clamp", ctypes.c_int), ("warm", ctypes.c_int)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_long), ("t", ctypes.c_double),
+                ("residual", ctypes.c_double), ("dt", ctypes.c_double),
+                ("converged", ctypes.c_int), ("windows", ctypes.c_long)]
+
+
+def build(force: bool = False) -> str:
+    """Compile hj_oracle.c into a shared library next to it (gcc, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        P = ctypes.POINTER
+        d = ctypes.c_double
+        _lib.or_solve.argtypes = [P(_Problem), P(_Opts), P(d), P(_Stats)]
+        _lib.or_solve.restype = ctypes.c_int
+        _lib.or_alpha.argtypes = [P(_Problem), P(d)]
+        _lib.or_cfl_dt.argtypes = [P(_Problem), d, P(d)]
+        _lib.or_cfl_dt.restype = d
+        _lib.or_hamiltonian.argtypes = [P(_Problem), P(d), P(d)]
+        _lib.or_hamiltonian.restype = d
+        _lib.or_margin.argtypes = [P(_Problem), P(d)]
+        _lib.or_margin.restype = d
+        _lib.or_fill_margin.argtypes = [P(_Problem), P(d)]
+        _lib.or_line_slopes.argtypes = [P(d), ctypes.c_long, d, ctypes.c_int, P(d), P(d)]
+        _lib.or_rhs.argtypes = [P(_Problem), ctypes.c_int, P(d), P(d)]
+        _lib.or_prolong.argtypes = [P(_Problem), P(d), P(_Problem), P(d)]
+        _lib.or_prolong.restype = ctypes.c_int
+        _lib.or_query_value.argtypes = [P(_Problem), P(d), ctypes.c_long, P(d), P(d)]
+        _lib.or_query_value.restype = ctypes.c_int
+        _lib.or_query_gradient.argtypes = [P(_Problem), P(d), ctypes.c_long, P(d), P(d)]
+        _lib.or_query_gradient.restype = ctypes.c_int
+        _lib.or_num_threads.restype = ctypes.c_int
+        _lib.or_set_num_threads.argtypes = [ctypes.c_int]
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _problem(spec) -> _Problem:
+    p = _Problem()
+    p.ndim = spec.ndim
+    for i in range(spec.ndim):
+        p.n[i] = spec.n[i]
+        p.lo[i] = spec.lo[i]
+        p.hi[i] = spec.hi[i]
+    p.model = _MODEL[spec.model]
+    for i, v in enumerate(spec.params):
+        p.params[i] = v
+    p.nd = len(spec.d_lo)
+    for i in range(p.nd):
+        p.d_lo[i] = spec.d_lo[i]
+        p.d_hi[i] = spec.d_hi[i]
+    p.con_kind = _CON[spec.con_kind]
+    for i, v in enumerate(spec.con_a):
+        p.con_a[i] = v
+    for i, v in enumerate(spec.con_b):
+        p.con_b[i] = v
+    return p
+
+
+def num_threads() -> int:
+    return lib().or_num_threads()
+
+
+def set_num_threads(k: int) -> None:
+    lib().or_set_num_threads(int(k))
+
+
+def solve(spec, scheme: int = 5, cfl: float = 0.5, dt: float = 0.0, tol: float = 1e-4,
+          check_dt: float = 0.1, max_steps: int = 0, fixed_steps: int = 0,
+          clamp: int = 0, warm: Optional[np.ndarray] = None) -> Tuple[np.ndarray, Dict]:
+    """Run the oracle solve; returns (W on the grid, stats)."""
+    W = np.zeros(spec.n, dtype=np.float64)
+    if warm is not None:
+        W[...] = warm
+    o = _Opts(scheme=scheme, cfl=cfl, dt=dt, tol=tol, check_dt=check_dt, max_steps=max_steps,
+              fixed_steps=fixed_steps, clamp=clamp, warm=1 if warm is not None else 0)
+    st = _Stats()
+    pr = _problem(spec)
+    rc = lib().or_solve(ctypes.byref(pr), ctypes.byref(o), _dp(W), ctypes.byref(st))
+    if rc < 0:
+        raise ValueError("oracle rejected the problem")
+    return W, dict(steps=st.steps, t=st.t, residual=st.residual, dt=st.dt,
+                   converged=bool(st.converged), windows=st.windows, rc=rc)
+
+
+def alpha(spec) -> np.ndarray:
+    a = np.zeros(spec.ndim)
+    pr = _problem(spec)
+    lib().or_alpha(ctypes.byref(pr), _dp(a))
+    return a
+
+
+def cfl_dt(spec, cfl: float = 0.5) -> float:
+    a = alpha(spec)
+    pr = _problem(spec)
+    return lib().or_cfl_dt(ctypes.byref(pr), cfl, _dp(a))
+
+
+def hamiltonian(spec, x: Sequence[float], p: Sequence[float]) -> float:
+    xa = np.ascontiguousarray(x, dtype=np.float64)
+    pa = np.ascontiguousarray(p, dtype=np.float64)
+    pr = _problem(spec)
+    return lib().or_hamiltonian(ctypes.byref(pr), _dp(xa), _dp(pa))
+
+
+def margin(spec) -> np.ndarray:
+    out = np.zeros(spec.n, dtype=np.float64)
+    pr = _problem(spec)
+    lib().or_fill_margin(ctypes.byref(pr), _dp(out))
+    return out
+
+
+def margin_at(spec, x: Sequence[float]) -> float:
+    xa = np.ascontiguousarray(x, dtype=np.float64)
+    pr = _problem(spec)
+    return lib().or_margin(ctypes.byref(pr), _dp(xa))
+
+
+def line_slopes(w: np.ndarray, h: float, scheme: int) -> Tuple[np.ndarray, np.ndarray]:
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    pm = np.zeros_like(w)
+    pp = np.zeros_like(w)
+    lib().or_line_slopes(_dp(w), w.size, h, scheme, _dp(pm), _dp(pp))
+    return pm, pp
+
+
+def rhs(spec, scheme: int, W: np.ndarray) -> np.ndarray:
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    out = np.zeros_like(W)
+    pr = _problem(spec)
+    lib().or_rhs(ctypes.byref(pr), scheme, _dp(W), _dp(out))
+    return out
+
+
+def prolong(coarse, Wc: np.ndarray, fine) -> np.ndarray:
+    Wc = np.ascontiguousarray(Wc, dtype=np.float64)
+    Wf = np.zeros(fine.n, dtype=np.float64)
+    pc, pf = _problem(coarse), _problem(fine)
+    if lib().or_prolong(ctypes.byref(pc), _dp(Wc), ctypes.byref(pf), _dp(Wf)) != 0:
+        raise ValueError("fine grid not inside coarse grid")
+    return Wf
+
+
+def query_value(spec, W: np.ndarray, xs: np.ndarray) -> np.ndarray:
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    xs = np.ascontiguousarray(xs, dtype=np.float64).reshape(-1, spec.ndim)
+    out = np.zeros(xs.shape[0])
+    pr = _problem(spec)
+    if lib().or_query_value(ctypes.byref(pr), _dp(W), xs.shape[0], _dp(xs), _dp(out)) != 0:
+        raise ValueError("query point outside the grid")
+    return out
+
+
+def query_gradient(spec, W: np.ndarray, xs: np.ndarray) -> np.ndarray:
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    xs = np.ascontiguousarray(xs, dtype=np.float64).reshape(-1, spec.ndim)
+    out = np.zeros_like(xs)
+    pr = _problem(spec)
+    if lib().or_query_gradient(ctypes.byref(pr), _dp(W), xs.shape[0], _dp(xs), _dp(out)) != 0:
+        raise ValueError("query point outside the grid")
+    return out
+
+
+# ------------------------------------------------------------------ brute force
+
+def _z_arc_extremes(z0, v0, a, tau):
+    """Min and max of z(t) = z0 + v0 t + a t^2 / 2 over t in [0, tau] (arrays)."""
+    z1 = z0 + v0 * tau + 0.5 * a * tau * tau
+    lo = np.minimum(z0, z1)
+    hi = np.maximum(z0, z1)
+    ts = np.where(a != 0.0, -v0 / np.where(a != 0.0, a, 1.0), -1.0)
+    inside = (ts > 0.0) & (ts < tau)
+    zs = z0 + v0 * ts + 0.5 * a * ts * ts
+    lo = np.where(inside, np.minimum(lo, zs), lo)
+    hi = np.where(inside, np.maximum(hi, zs), hi)
+    return lo, hi
+
+
+def brute_force_z(z0: np.ndarray, v0: np.ndarray, horizon: float, intervals: int,
+                  kT: float, g: float, u_set: Sequence[float], d_set: Sequence[float],
+                  zlo: float, zhi: float, disturbance_last: bool) -> np.ndarray:
+    """Value of the discrete game W = inf_d sup_u min_t l(z(t)) for the 2-D
+    double integrator with piecewise-constant inputs drawn from finite sets.
+
+    disturbance_last=True: in every interval the disturbance picks after
+    seeing the control (max_u min_d per interval) -- the disturbance's
+    information advantage, giving the lower bracket.  False: the control
+    picks after the disturbance (min_d max_u), the upper bracket.
+    The margin l(z) = min(z - zlo, zhi - z) is evaluated exactly along each
+    arc via the arc's extreme heights (l is concave in z).
+    """
+    tau = horizon / intervals
+
+    def margin_of(z):
+        return np.minimum(z - zlo, zhi - z)
+
+    def rec(z, v, m, depth):
+        if depth == intervals:
+            return m
+        outs_u = []
+        for u in u_set:
+            outs_d = []
+            for d in d_set:
+                a = kT * u - g + d
+                lo, hi = _z_arc_extremes(z, v, a, tau)
+                m2 = np.minimum(m, np.minimum(margin_of(lo), margin_of(hi)))
+                z2 = z + v * tau + 0.5 * a * tau * tau
+                v2 = v + a * tau
+                outs_d.append((u, d, z2, v2, m2))
+            outs_u.append(outs_d)
+        if disturbance_last:
+            best = None
+            for outs_d in outs_u:
+                worst = None
+                for (_, _, z2, v2, m2) in outs_d:
+                    r = rec(z2, v2, m2, depth + 1)
+                    worst = r if worst is None else np.minimum(worst, r)
+                best = worst if best is None else np.maximum(best, worst)
+            return best
+        # control last: min over d of max over u
+        worst = None
+        for j in range(len(d_set)):
+            best = None
+            for outs_d in outs_u:
+                (_, _, z2, v2, m2) = outs_d[j]
+                r = rec(z2, v2, m2, depth + 1)
+                best = r if best is None else np.maximum(best, r)
+            worst = best if worst is None else np.minimum(worst, best)
+        return worst
+
+    z0 = np.asarray(z0, dtype=np.float64)
+    v0 = np.asarray(v0, dtype=np.float64)
+    return rec(z0, v0, margin_of(z0), 0)
+
+
+def z_closed_form(z: np.ndarray, v: np.ndarray, kT: float, g: float, u_hi: float,
+                  u_lo: float, b: float, zlo: float, zhi: float) -> np.ndarray:
+    """Converged value of the 2-D double integrator against worst-case wind:
+    the distance left to the nearer wall after braking at full authority."""
+    a_up = kT * u_hi - g - b  # best upward acceleration under the worst wind
+    a_dn = g - kT * u_lo - b  # best downward acceleration magnitude
+    lo_side = z - zlo - np.where(v < 0.0, v * v / (2.0 * a_up), 0.0)
+    hi_side = zhi - z - np.where(v > 0.0, v * v / (2.0 * a_dn), 0.0)
+    return np.minimum(lo_side, hi_side)
+
+
+__all__ = ["build", "lib", "solve", "alpha", "cfl_dt", "hamiltonian", "margin", "margin_at",
+           "line_slopes", "rhs", "prolong", "query_value", "query_gradient", "brute_force_z",
+           "z_closed_form", "num_threads", "set_num_threads"]
+
