@@ -1,0 +1,218 @@
+/*
+ * hj.h -- C ABI of the GB300 (sm_103a) Hamilton-Jacobi safe-set library.
+ *
+ * The library computes the safe sets of Herbert, Choi et al., "Scalable
+ * Learning of Safety Guarantees for Autonomous Systems using Hamilton-Jacobi
+ * Reachability" (arXiv 2101.05916):
+ *   - the value function of Sec. II-A, Eq. 1,
+ *   - obtained by iterating the HJI variational inequality of Eq. 2 backward
+ *     in time until convergence,
+ *   - on one grid per decomposed subsystem (Sec. III-A),
+ *   - warm-started from a previous value function (Sec. III-B),
+ *   - or from a coarse-grid solution migrated to a finer grid (Sec. III-C).
+ *
+ * Sign convention.  Everything here uses W := -V and l := -c, where V and c
+ * are the paper's value and constraint functions.  So:
+ *   - l is positive inside the constraint set;
+ *   - the safe set is {W >= 0};
+ *   - the control maximises and the disturbance minimises;
+ *   - the clamp of Eq. 2 reads W <- min(W, l).
+ * Negate the results to get the paper's V.
+ *
+ * Discretisation (the paper names none; this is the textbook scheme):
+ *   - Grid: uniform, n[i] nodes from lo[i] to hi[i] inclusive.  Row-major
+ *     with the LAST axis fastest.  Values are FP32.  Ghost nodes continue
+ *     each grid line linearly through its two outermost nodes.
+ *   - Slopes: first-order upwind, ENO2 or WENO5 one-sided differences.
+ *   - Hamiltonian: global Lax-Friedrichs numerical Hamiltonian, with bang-bang
+ *     control and worst-case disturbance.
+ *   - Time step: dt = cfl / sum_i(a_i / h_i), where a_i is the largest |f_i|
+ *     over the grid and the input boxes.
+ *   - Integration: TVD-RK3, then the clamp after each full step.
+ *   - Stop: when max|W(t + check_dt) - W(t)| < tol.
+ *
+ * Threading and memory:
+ *   - Handles are not thread-safe.  Use one handle per thread, or serialise
+ *     the calls.
+ *   - Device memory belongs to the library.
+ *   - Host arrays belong to the caller.  They are read or written only during
+ *     the call.
+ *   - Every call returns an hj_status.  On failure, hj_last_error() gives a
+ *     thread-local message.
+ *   - Nothing falls back to the CPU: with no usable CUDA device, every
+ *     computing call returns HJ_ERR_CUDA.
+ */
+#ifndef HJ_H
+#define HJ_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hj_grid_s* hj_grid;
+
+typedef enum {
+  HJ_OK = 0,
+  HJ_ERR_ARG = 1,           /* invalid argument (null pointer, bad size, out-of-grid query) */
+  HJ_ERR_OOM = 2,           /* device allocation failed                                    */
+  HJ_ERR_CUDA = 3,          /* a CUDA call failed, or no device                             */
+  HJ_ERR_NOT_CONVERGED = 4, /* step cap or wall-time cap hit.  W is still the valid         */
+                            /* finite-horizon value after the steps taken                   */
+  HJ_ERR_STATE = 5,         /* e.g. warm solve with no prior, or dynamics/constraint unset  */
+  HJ_ERR_ABORTED = 6,       /* cancelled between check windows                              */
+  HJ_ERR_DIVERGED = 7       /* a non-finite value appeared in W                             */
+} hj_status;
+
+/* Dynamics f(x, u, d) (Sec. II-A).  The parameter vector is per model.
+ *   HJ_DRIFT   any ndim 1..4.  f = d.  One disturbance input per axis.  No params.
+ *   HJ_QUAD_Z  ndim 2, state (z, vz).  f = (vz, kT u - g + d).
+ *              params = {kT, g, u_lo, u_hi}.  One disturbance input.
+ *              This is the 2-D vertical quadcopter (Sec. V-A) and the z block
+ *              of Eq. 3.
+ *   HJ_QUAD_X4 ndim 4, state (p, v, th, w).
+ *              f = (v, g tan th, -d1 th + w, -d0 th + n0 u), with the single
+ *              disturbance d added to component `axis` (0 or 1).
+ *              params = {g, d1, d0, n0, u_lo, u_hi, axis}.
+ *              This is the x (or y) block of Eq. 3. */
+enum { HJ_DRIFT = 0, HJ_QUAD_Z = 1, HJ_QUAD_X4 = 2 };
+
+/* spatial schemes */
+enum { HJ_FIRST = 1, HJ_ENO2 = 2, HJ_WENO5 = 5 };
+/* clamp after each step: VI = min(W, l) (Eq. 2); MONOTONE = min(W, l, W_prev) */
+enum { HJ_CLAMP_VI = 0, HJ_CLAMP_MONOTONE = 1 };
+/* initial value: COLD = l (Eq. 2 terminal value); WARM = min(prior, l) (Sec. III-B) */
+enum { HJ_COLD = 0, HJ_WARM = 1 };
+
+#define HJ_MAX_DIM 4
+
+typedef struct {
+  int scheme;            /* HJ_FIRST, HJ_ENO2 or HJ_WENO5 (default WENO5)                 */
+  double cfl;            /* Courant number (default 0.5)                                  */
+  double dt;             /* > 0: fixed step instead of the CFL rule (default 0)           */
+  double tol;            /* stop when the L-inf change over a window is below (1e-4)      */
+  double check_dt;       /* window length in simulated seconds (default 0.1)              */
+  long long max_steps;   /* step cap, 0 = none (default 1000000)                          */
+  long long fixed_steps; /* > 0: run exactly this many steps and skip the stop test       */
+  double max_wall_ms;    /* wall-time cap checked between windows, 0 = none               */
+  int clamp;             /* HJ_CLAMP_VI (default) or HJ_CLAMP_MONOTONE                    */
+  int use_graph;         /* 1: replay each window as a captured CUDA graph (default 1)    */
+} hj_solve_opts;
+
+typedef struct {
+  long long steps;   /* TVD-RK3 steps taken                                   */
+  double t;          /* simulated backward time reached                       */
+  double residual;   /* L-inf change over the last window                     */
+  double dt;         /* step used                                             */
+  double wall_ms;    /* host wall time of the call                            */
+  int converged;     /* 1 if residual < tol                                   */
+  long long windows; /* stop tests performed                                  */
+} hj_solve_stats;
+
+/* Fill *o with the defaults listed above. */
+void hj_default_opts(hj_solve_opts* o);
+
+/* Create a grid of ndim (1..4) axes.  Axis i has n[i] >= 3 nodes spanning
+ * [lo[i], hi[i]], with lo < hi.  The total node count must be below 2^31.
+ * cuda_stream is a cudaStream_t, or NULL for the legacy default stream.  All
+ * device work of this handle is ordered on that stream.  This call allocates
+ * four FP32 fields (W, two RK stages, the window snapshot) of n[0]*..*n[ndim-1]
+ * values each on the current device.
+ * Errors: HJ_ERR_ARG on bad sizes, HJ_ERR_OOM, HJ_ERR_CUDA. */
+hj_status hj_grid_create(hj_grid* out, int ndim, const int* n, const double* lo,
+                         const double* hi, void* cuda_stream);
+void hj_grid_destroy(hj_grid g);
+hj_status hj_set_stream(hj_grid g, void* cuda_stream);
+
+/* Dynamics of Sec. II-A (and Eq. 3 for the quadcopter blocks).  params has
+ * nparams entries, laid out per model as in the model list above.
+ * HJ_ERR_ARG on an unknown model, a wrong ndim or too few parameters. */
+hj_status hj_set_dynamics(hj_grid g, int model, const double* params, int nparams);
+
+/* Constraint set C of Sec. II-A, as the margin l = -c, where c is the signed
+ * distance to C.  The safe region is the box lo[i] <= x_i <= hi[i].  An axis
+ * with both bounds infinite is unconstrained.  Distances are in raw state
+ * units:
+ *   - inside the box, l is the distance to the nearest face;
+ *   - outside it, l is minus the Euclidean distance to the box.
+ * At least one axis must be constrained. */
+hj_status hj_set_constraint(hj_grid g, const double* box_lo, const double* box_hi);
+/* Alternative constraint: the safe region lies outside a ball.
+ * l = |x - centre| - radius, with radius > 0. */
+hj_status hj_set_constraint_ball(hj_grid g, const double* centre, double radius);
+
+/* Disturbance box D (Sec. II-C): d_j in [d_lo[j], d_hi[j]] for each of the
+ * nd inputs.  Asymmetric intervals are allowed; they come from a GP
+ * confidence interval.  nd must match the model: 1 for the quadcopter
+ * blocks, ndim for HJ_DRIFT. */
+hj_status hj_set_disturbance_bound(hj_grid g, const double* d_lo, const double* d_hi, int nd);
+
+/* Iterate Eq. 2 to convergence.
+ * Starting value:
+ *   - HJ_COLD starts from l.
+ *   - HJ_WARM starts from min(prior, l) (Sec. III-B).  The prior is the
+ *     grid's current W: the last result, the last hj_set_value, or the last
+ *     hj_prolong into this grid.
+ * o may be NULL, which means the defaults.  s may be NULL.
+ * On HJ_OK or HJ_ERR_NOT_CONVERGED the grid's W holds the result.
+ * Returns:
+ *   HJ_ERR_STATE    when dynamics, constraint or disturbance are unset, or
+ *                   HJ_WARM is asked with no prior;
+ *   HJ_ERR_DIVERGED when a non-finite value appears. */
+hj_status hj_solve(hj_grid g, int mode, const hj_solve_opts* o, hj_solve_stats* s);
+
+/* Solve several grids together (Sec. III-A: decomposed subsystems are
+ * independent).  Each time step of all still-unconverged grids is one fused
+ * launch per RK stage; each grid keeps its own dt and stop test.  All grids
+ * must be on the same device.  The work runs on the stream of gs[0].  modes,
+ * opts and stats are arrays of ngrids entries.  opts may be NULL, or point to
+ * a single entry when opts_count is 1.  Returns the first non-OK status, in
+ * grid order; each grid's own status goes to status_out when that is
+ * non-NULL. */
+hj_status hj_solve_batch(hj_grid* gs, int ngrids, const int* modes, const hj_solve_opts* opts,
+                         int opts_count, hj_solve_stats* stats, int* status_out);
+
+/* Coarse-to-fine migration (Sec. III-C): fine.W = min(interp(coarse.W), l_fine),
+ * where interp is multilinear interpolation of the coarse W at the fine nodes.
+ * Both grids need the same ndim, and the fine box must lie inside the coarse
+ * box.  The fine grid needs its constraint set first.  Afterwards an HJ_WARM
+ * solve of the fine grid starts from the migrated value. */
+hj_status hj_prolong(hj_grid coarse, hj_grid fine);
+
+/* Copy a dense row-major FP32 field of npts values into W (a prior, or a
+ * resume point), or W out of the library.  on_device = 1 means the pointer
+ * is device memory on the grid's device; on_device = 0 means host memory.
+ * Both calls return after the copy has completed. */
+hj_status hj_set_value(hj_grid g, const float* src, int on_device);
+hj_status hj_get_value(hj_grid g, float* dst, int on_device);
+
+/* W (hj_query_value) or grad W (hj_query_gradient) at npts arbitrary states.
+ * x is host memory with npts * ndim doubles, row-major (point-major).
+ *   - Values are the multilinear interpolation of W.
+ *   - Gradients are the multilinear interpolation of the node gradients.
+ *     Node gradients are central differences, one-sided at the ends of an
+ *     axis.  grad_out holds npts * ndim doubles.
+ * The gradient gives the safety control u* = argmax_u grad W . f
+ * (Sec. II-A, in the W convention).
+ * HJ_ERR_ARG if a point lies outside the grid box. */
+hj_status hj_query_value(hj_grid g, int npts, const double* x, double* v_out);
+hj_status hj_query_gradient(hj_grid g, int npts, const double* x, double* grad_out);
+
+/* Largest |f_i| over the grid and the input boxes, per axis.  These are the
+ * Lax-Friedrichs coefficients, and the CFL dt follows from them.  Computed on
+ * the device by a max-reduction.  alpha_out has ndim entries. */
+hj_status hj_alpha(hj_grid g, double* alpha_out);
+
+/* Number of nodes of the grid. */
+long long hj_grid_points(hj_grid g);
+
+/* Thread-local message describing the last failure of this thread. */
+const char* hj_last_error(void);
+
+/* Number of kernels this library has launched in the process so far.
+ * Graph replays count each kernel node. */
+unsigned long long hj_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HJ_H */

@@ -1,0 +1,554 @@
+// hj_api.cu -- C ABI of the HJ safe-set library: grid lifecycle, problem set-up,
+// the single-grid solve driver, prolongation, value I/O and queries.
+//
+// Solve driver (Eq. 2 iterated "until convergence", Sec. II-A):
+//   init kernel (W = l, or min(prior, l))
+//   -> alpha max-reduction, read back once; dt = cfl / sum a_i / h_i
+//   -> repeat check windows of ceil(check_dt / dt) TVD-RK3 steps.  Each step
+//      is three stage launches.  The last stage of a window also folds
+//      max |W - W_window_start| into a device scalar.  That scalar is the
+//      only value read back per window.
+// A window is captured once as a CUDA graph and replayed, so the launch cost
+// of the many small kernels of a 2-D grid is paid once per graph.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "hj_grid.h"
+
+namespace hja {
+
+static thread_local char t_err[1024] = "";
+
+hj_status fail(hj_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(t_err, sizeof(t_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+hjd::DevGrid devgrid(const hj_grid g) {
+  hjd::DevGrid d;
+  std::memset(&d, 0, sizeof(d));
+  d.ndim = g->ndim;
+  long long s = 1;
+  for (int i = g->ndim - 1; i >= 0; --i) {
+    d.n[i] = g->n[i];
+    d.stride[i] = (int)s;
+    s *= g->n[i];
+  }
+  d.npts = (int)g->npts;
+  d.plane = g->ndim >= 2 ? g->n[g->ndim - 2] * g->n[g->ndim - 1] : g->n[0];
+  for (int i = 0; i < g->ndim; ++i) {
+    d.lo[i] = (float)g->lo[i];
+    d.h[i] = (float)g->h[i];
+    d.lo_d[i] = g->lo[i];
+    d.h_d[i] = g->h[i];
+    d.ih[i] = (float)(1.0 / g->h[i]);
+    d.ih6[i] = (float)(1.0 / (6.0 * g->h[i]));
+    d.wfloor[i] = (float)(1e-18 * g->h[i] * g->h[i]);
+  }
+  d.model = g->model;
+  for (int i = 0; i < 8; ++i) d.prm[i] = (float)g->params[i];
+  for (int i = 0; i < HJ_MAX_DIM; ++i) {
+    d.dlo[i] = (float)g->d_lo[i];
+    d.dhi[i] = (float)g->d_hi[i];
+  }
+  d.con_kind = g->con_kind;
+  d.con_mask = 0;
+  for (int i = 0; i < g->ndim; ++i) {
+    d.ca[i] = (float)g->ca[i];
+    d.cb[i] = (float)g->cb[i];
+    if (g->con_kind == hjd::C_BOX && !(std::isinf(g->ca[i]) && std::isinf(g->cb[i])))
+      d.con_mask |= 1u << i;
+  }
+  for (int i = 0; i < HJ_MAX_DIM; ++i) d.alpha[i] = g->alpha[i];
+  d.tab = g->tab;
+  return d;
+}
+
+static int required_nd(const hj_grid g) { return g->model == HJ_DRIFT ? g->ndim : 1; }
+
+hj_status validate_ready(hj_grid g, int scheme) {
+  if (g->model < 0) return fail(HJ_ERR_STATE, "dynamics not set");
+  if (g->con_kind < 0) return fail(HJ_ERR_STATE, "constraint not set");
+  if (g->nd != required_nd(g))
+    return fail(HJ_ERR_STATE, "disturbance bound not set (model needs %d intervals, have %d)",
+                required_nd(g), g->nd);
+  if (!hjk::stage_supported(g->model, g->ndim, scheme))
+    return fail(HJ_ERR_ARG, "scheme %d not available for model %d in %d-D", scheme, g->model,
+                g->ndim);
+  return HJ_OK;
+}
+
+hj_status ensure_alpha(hj_grid g) {
+  if (g->alpha_valid) return HJ_OK;
+  HJ_CU(cudaMemsetAsync(g->dscal, 0, 4 * sizeof(unsigned), g->stream));
+  hjd::DevGrid d = devgrid(g);
+  HJ_CU(hjk::launch_alpha(d, g->dscal, g->stream));
+  HJ_CU(cudaMemcpyAsync(g->hscal, g->dscal, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost,
+                        g->stream));
+  HJ_CU(cudaStreamSynchronize(g->stream));
+  for (int i = 0; i < g->ndim; ++i) {
+    unsigned b = g->hscal[i];
+    float f;
+    std::memcpy(&f, &b, 4);
+    g->alpha[i] = f;
+  }
+  g->alpha_valid = true;
+  return HJ_OK;
+}
+
+double cfl_dt(const hj_grid g, double cfl) {
+  double s = 0.0;
+  for (int i = 0; i < g->ndim; ++i) s += (double)g->alpha[i] / g->h[i];
+  return s > 0.0 ? cfl / s : 0.0;
+}
+
+static void drop_graph(hj_grid g) {
+  if (g->gexec) cudaGraphExecDestroy(g->gexec);
+  g->gexec = nullptr;
+  g->g_per = 0;
+}
+
+static void invalidate(hj_grid g) {
+  g->alpha_valid = false;
+  drop_graph(g);
+}
+
+// k TVD-RK3 steps; the last one folds the window residual when check_last.
+static cudaError_t enqueue_steps(hj_grid g, const hjd::DevGrid& d, int scheme, int clamp,
+                                 float dt, long long k, bool check_last, cudaStream_t s) {
+  hjd::StageArgs a1{g->W, g->W, g->A, nullptr, nullptr, dt, 0, clamp};
+  hjd::StageArgs a2{g->A, g->W, g->B, nullptr, nullptr, dt, 0, clamp};
+  hjd::StageArgs a3{g->B, g->W, g->W, g->snap, g->dscal + 4, dt, 0, clamp};
+  for (long long i = 0; i < k; ++i) {
+    cudaError_t e;
+    if ((e = hjk::launch_stage(d, scheme, 1, a1, s)) != cudaSuccess) return e;
+    if ((e = hjk::launch_stage(d, scheme, 2, a2, s)) != cudaSuccess) return e;
+    a3.check = (check_last && i == k - 1) ? 1 : 0;
+    if ((e = hjk::launch_stage(d, scheme, 3, a3, s)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// One check window: reset the residual, k steps, copy the residual to pinned host memory.
+static cudaError_t enqueue_window(hj_grid g, const hjd::DevGrid& d, int scheme, int clamp, float dt,
+                                  long long k, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(g->dscal + 4, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  if ((e = enqueue_steps(g, d, scheme, clamp, dt, k, true, s)) != cudaSuccess) return e;
+  return cudaMemcpyAsync(g->hscal + 4, g->dscal + 4, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+}
+
+static hj_status run_window(hj_grid g, const hjd::DevGrid& d, int scheme, int clamp, float dt,
+                            long long k, bool use_graph) {
+  if (use_graph && k <= 4096) {
+    if (!(g->gexec && g->g_per == k && g->g_dt == dt && g->g_scheme == scheme &&
+          g->g_clamp == clamp)) {
+      drop_graph(g);
+      cudaGraph_t graph = nullptr;
+      HJ_CU(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
+      unsigned long long before = hjk::g_launches.load();
+      cudaError_t e = enqueue_window(g, d, scheme, clamp, dt, k, g->cap_stream);
+      cudaError_t e2 = cudaStreamEndCapture(g->cap_stream, &graph);
+      // launches recorded during capture run later, on replay
+      hjk::g_launches.store(before);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail(HJ_ERR_CUDA, "graph capture failed: %s",
+                    cudaGetErrorString(e != cudaSuccess ? e : e2));
+      }
+      cudaError_t e3 = cudaGraphInstantiate(&g->gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e3 != cudaSuccess) {
+        g->gexec = nullptr;
+        return fail(HJ_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e3));
+      }
+      g->g_per = k;
+      g->g_dt = dt;
+      g->g_scheme = scheme;
+      g->g_clamp = clamp;
+    }
+    HJ_CU(cudaGraphLaunch(g->gexec, g->stream));
+    hjk::g_launches.fetch_add(3ull * (unsigned long long)k);
+  } else {
+    HJ_CU(enqueue_window(g, d, scheme, clamp, dt, k, g->stream));
+  }
+  HJ_CU(cudaStreamSynchronize(g->stream));
+  return HJ_OK;
+}
+
+static float bits_to_float(unsigned b) {
+  float f;
+  std::memcpy(&f, &b, 4);
+  return f;
+}
+
+}  // namespace hja
+
+using namespace hja;
+
+extern "C" {
+
+const char* hj_last_error(void) { return t_err; }
+
+unsigned long long hj_kernel_launches(void) { return hjk::g_launches.load(); }
+
+long long hj_grid_points(hj_grid g) { return g ? g->npts : 0; }
+
+void hj_default_opts(hj_solve_opts* o) {
+  if (!o) return;
+  o->scheme = HJ_WENO5;
+  o->cfl = 0.5;
+  o->dt = 0.0;
+  o->tol = 1e-4;
+  o->check_dt = 0.1;
+  o->max_steps = 1000000;
+  o->fixed_steps = 0;
+  o->max_wall_ms = 0.0;
+  o->clamp = HJ_CLAMP_VI;
+  o->use_graph = 1;
+}
+
+void hj_grid_destroy(hj_grid g) {
+  if (!g) return;
+  {
+    DeviceGuard dg(g->device);
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    drop_graph(g);
+    cudaFree(g->W);
+    cudaFree(g->A);
+    cudaFree(g->B);
+    cudaFree(g->snap);
+    cudaFree(g->tab);
+    cudaFree(g->dscal);
+    cudaFree(g->qbuf);
+    if (g->hscal) cudaFreeHost(g->hscal);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+  }
+  delete g;
+}
+
+hj_status hj_grid_create(hj_grid* out, int ndim, const int* n, const double* lo, const double* hi,
+                         void* cuda_stream) {
+  if (!out) return fail(HJ_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (ndim < 1 || ndim > HJ_MAX_DIM) return fail(HJ_ERR_ARG, "ndim must be 1..%d", HJ_MAX_DIM);
+  if (!n || !lo || !hi) return fail(HJ_ERR_ARG, "n/lo/hi is NULL");
+  long long npts = 1;
+  for (int i = 0; i < ndim; ++i) {
+    if (n[i] < 3) return fail(HJ_ERR_ARG, "axis %d has %d nodes (need >= 3)", i, n[i]);
+    if (!(hi[i] > lo[i]) || !std::isfinite(lo[i]) || !std::isfinite(hi[i]))
+      return fail(HJ_ERR_ARG, "axis %d: need finite lo < hi", i);
+    npts *= n[i];
+    if (npts >= (1ll << 31)) return fail(HJ_ERR_ARG, "grid has 2^31 or more nodes");
+  }
+  int dev = 0;
+  int count = 0;
+  cudaError_t ce = cudaGetDeviceCount(&count);
+  if (ce != cudaSuccess || count == 0)
+    return fail(HJ_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(ce));
+  HJ_CU(cudaGetDevice(&dev));
+  hj_grid g = new (std::nothrow) hj_grid_s();
+  if (!g) return fail(HJ_ERR_OOM, "host allocation failed");
+  g->device = dev;
+  g->ndim = ndim;
+  g->npts = npts;
+  for (int i = 0; i < ndim; ++i) {
+    g->n[i] = n[i];
+    g->lo[i] = lo[i];
+    g->hi[i] = hi[i];
+    g->h[i] = (hi[i] - lo[i]) / (double)(n[i] - 1);
+  }
+  g->stream = (cudaStream_t)cuda_stream;
+  size_t bytes = (size_t)npts * sizeof(float);
+  bytes = (bytes + 255) & ~(size_t)255;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMalloc(&g->W, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&g->A, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&g->B, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&g->snap, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&g->dscal, 64 * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMallocHost(&g->hscal, 64 * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    hj_status st = fail(e == cudaErrorMemoryAllocation ? HJ_ERR_OOM : HJ_ERR_CUDA,
+                        "grid allocation (%lld nodes): %s", npts, cudaGetErrorString(e));
+    cudaGetLastError();
+    hj_grid_destroy(g);
+    return st;
+  }
+  *out = g;
+  return HJ_OK;
+}
+
+hj_status hj_set_stream(hj_grid g, void* cuda_stream) {
+  if (!g) return fail(HJ_ERR_ARG, "grid is NULL");
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  g->stream = (cudaStream_t)cuda_stream;
+  return HJ_OK;
+}
+
+hj_status hj_set_dynamics(hj_grid g, int model, const double* params, int nparams) {
+  if (!g) return fail(HJ_ERR_ARG, "grid is NULL");
+  if (nparams < 0 || (nparams > 0 && !params)) return fail(HJ_ERR_ARG, "bad parameter vector");
+  if (nparams > 8) return fail(HJ_ERR_ARG, "at most 8 parameters");
+  if (model == HJ_QUAD_Z) {
+    if (g->ndim != 2) return fail(HJ_ERR_ARG, "HJ_QUAD_Z needs a 2-D grid");
+    if (nparams < 4) return fail(HJ_ERR_ARG, "HJ_QUAD_Z needs {kT, g, u_lo, u_hi}");
+    if (!(params[2] <= params[3])) return fail(HJ_ERR_ARG, "u_lo > u_hi");
+  } else if (model == HJ_QUAD_X4) {
+    if (g->ndim != 4) return fail(HJ_ERR_ARG, "HJ_QUAD_X4 needs a 4-D grid");
+    if (nparams < 7) return fail(HJ_ERR_ARG, "HJ_QUAD_X4 needs {g, d1, d0, n0, u_lo, u_hi, axis}");
+    if (!(params[4] <= params[5])) return fail(HJ_ERR_ARG, "u_lo > u_hi");
+    if (params[6] != 0.0 && params[6] != 1.0) return fail(HJ_ERR_ARG, "axis must be 0 or 1");
+    double th_max = std::max(std::fabs(g->lo[2]), std::fabs(g->hi[2]));
+    if (th_max >= 1.5) return fail(HJ_ERR_ARG, "theta range must stay inside (-1.5, 1.5) rad");
+  } else if (model != HJ_DRIFT) {
+    return fail(HJ_ERR_ARG, "unknown model %d", model);
+  }
+  for (int i = 0; i < 8; ++i) g->params[i] = (i < nparams) ? params[i] : 0.0;
+  g->model = model;
+  DeviceGuard dg(g->device);
+  if (model == HJ_QUAD_X4) {
+    // g * tan(th_j) for every th node, in double, rounded once to float
+    int m = g->n[2];
+    float* host = new float[m];
+    for (int j = 0; j < m; ++j) host[j] = (float)(params[0] * std::tan(g->lo[2] + j * g->h[2]));
+    cudaFree(g->tab);
+    g->tab = nullptr;
+    cudaError_t e = cudaMalloc(&g->tab, m * sizeof(float));
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(g->tab, host, m * sizeof(float), cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    delete[] host;
+    if (e != cudaSuccess) return fail(HJ_ERR_CUDA, "table upload: %s", cudaGetErrorString(e));
+  }
+  invalidate(g);
+  return HJ_OK;
+}
+
+hj_status hj_set_constraint(hj_grid g, const double* box_lo, const double* box_hi) {
+  if (!g) return fail(HJ_ERR_ARG, "grid is NULL");
+  if (!box_lo || !box_hi) return fail(HJ_ERR_ARG, "box is NULL");
+  int constrained = 0;
+  for (int i = 0; i < g->ndim; ++i) {
+    if (std::isnan(box_lo[i]) || std::isnan(box_hi[i]) || !(box_lo[i] <= box_hi[i]))
+      return fail(HJ_ERR_ARG, "axis %d: need box_lo <= box_hi", i);
+    if (!(std::isinf(box_lo[i]) && std::isinf(box_hi[i]))) constrained++;
+  }
+  if (!constrained) return fail(HJ_ERR_ARG, "no axis is constrained");
+  g->con_kind = hjd::C_BOX;
+  for (int i = 0; i < g->ndim; ++i) {
+    g->ca[i] = box_lo[i];
+    g->cb[i] = box_hi[i];
+  }
+  drop_graph(g);
+  return HJ_OK;
+}
+
+hj_status hj_set_constraint_ball(hj_grid g, const double* centre, double radius) {
+  if (!g) return fail(HJ_ERR_ARG, "grid is NULL");
+  if (!centre || !(radius > 0.0) || !std::isfinite(radius))
+    return fail(HJ_ERR_ARG, "need a centre and a finite radius > 0");
+  g->con_kind = hjd::C_BALL_OUT;
+  for (int i = 0; i < g->ndim; ++i) {
+    if (!std::isfinite(centre[i])) return fail(HJ_ERR_ARG, "centre must be finite");
+    g->ca[i] = centre[i];
+    g->cb[i] = 0.0;
+  }
+  g->cb[0] = radius;
+  drop_graph(g);
+  return HJ_OK;
+}
+
+hj_status hj_set_disturbance_bound(hj_grid g, const double* d_lo, const double* d_hi, int nd) {
+  if (!g) return fail(HJ_ERR_ARG, "grid is NULL");
+  if (nd < 1 || nd > HJ_MAX_DIM || !d_lo || !d_hi) return fail(HJ_ERR_ARG, "bad disturbance box");
+  for (int i = 0; i < nd; ++i)
+    if (!std::isfinite(d_lo[i]) || !std::isfinite(d_hi[i]) || d_lo[i] > d_hi[i])
+      return fail(HJ_ERR_ARG, "input %d: need finite d_lo <= d_hi", i);
+  g->nd = nd;
+  for (int i = 0; i < HJ_MAX_DIM; ++i) {
+    g->d_lo[i] = i < nd ? d_lo[i] : 0.0;
+    g->d_hi[i] = i < nd ? d_hi[i] : 0.0;
+  }
+  invalidate(g);
+  return HJ_OK;
+}
+
+hj_status hj_alpha(hj_grid g, double* alpha_out) {
+  if (!g || !alpha_out) return fail(HJ_ERR_ARG, "NULL argument");
+  if (g->model < 0) return fail(HJ_ERR_STATE, "dynamics not set");
+  if (g->nd != (g->model == HJ_DRIFT ? g->ndim : 1)) return fail(HJ_ERR_STATE, "bound not set");
+  DeviceGuard dg(g->device);
+  hj_status st = ensure_alpha(g);
+  if (st != HJ_OK) return st;
+  for (int i = 0; i < g->ndim; ++i) alpha_out[i] = g->alpha[i];
+  return HJ_OK;
+}
+
+hj_status hj_solve(hj_grid g, int mode, const hj_solve_opts* o_in, hj_solve_stats* s) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (!g) return fail(HJ_ERR_ARG, "grid is NULL");
+  hj_solve_opts o;
+  hj_default_opts(&o);
+  if (o_in) o = *o_in;
+  if (mode != HJ_COLD && mode != HJ_WARM) return fail(HJ_ERR_ARG, "mode must be HJ_COLD or HJ_WARM");
+  if (!(o.cfl > 0.0) || !(o.tol >= 0.0) || !(o.check_dt > 0.0) || o.dt < 0.0)
+    return fail(HJ_ERR_ARG, "bad solve options");
+  if (o.clamp != HJ_CLAMP_VI && o.clamp != HJ_CLAMP_MONOTONE) return fail(HJ_ERR_ARG, "bad clamp");
+  hj_status st = validate_ready(g, o.scheme);
+  if (st != HJ_OK) return st;
+  if (mode == HJ_WARM && !g->has_value)
+    return fail(HJ_ERR_STATE, "warm start asked but the grid holds no prior value");
+  DeviceGuard dg(g->device);
+  hj_solve_stats stats;
+  std::memset(&stats, 0, sizeof(stats));
+
+  if ((st = ensure_alpha(g)) != HJ_OK) return st;
+  double dt = o.dt > 0.0 ? o.dt : cfl_dt(g, o.cfl);
+  stats.dt = dt;
+  hjd::DevGrid d = devgrid(g);
+  HJ_CU(hjk::launch_init(d, g->W, g->snap, mode == HJ_WARM ? 1 : 0, g->stream));
+  g->has_value = true;
+  hj_status rc = HJ_OK;
+  float fdt = (float)dt;
+  if (dt <= 0.0) {
+    // nothing moves: the initial value is the fixed point
+    HJ_CU(cudaStreamSynchronize(g->stream));
+    stats.converged = 1;
+  } else if (o.fixed_steps > 0) {
+    HJ_CU(enqueue_steps(g, d, o.scheme, o.clamp, fdt, o.fixed_steps, false, g->stream));
+    HJ_CU(cudaStreamSynchronize(g->stream));
+    stats.steps = o.fixed_steps;
+  } else {
+    long long per = (long long)std::ceil(o.check_dt / dt - 1e-9);
+    if (per < 1) per = 1;
+    for (;;) {
+      long long todo = per;
+      if (o.max_steps > 0 && stats.steps + todo > o.max_steps) todo = o.max_steps - stats.steps;
+      st = run_window(g, d, o.scheme, o.clamp, fdt, todo, o.use_graph != 0 && todo == per);
+      if (st != HJ_OK) return st;
+      stats.steps += todo;
+      stats.windows += 1;
+      float r = bits_to_float(g->hscal[4]);
+      stats.residual = r;
+      if (!std::isfinite(r)) {
+        rc = fail(HJ_ERR_DIVERGED, "non-finite value after %lld steps", stats.steps);
+        break;
+      }
+      if ((double)r < o.tol) {
+        stats.converged = 1;
+        break;
+      }
+      if (o.max_steps > 0 && stats.steps >= o.max_steps) {
+        rc = fail(HJ_ERR_NOT_CONVERGED, "step cap %lld reached (residual %g)", o.max_steps,
+                  (double)r);
+        break;
+      }
+      double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                      .count();
+      if (o.max_wall_ms > 0.0 && ms > o.max_wall_ms) {
+        rc = fail(HJ_ERR_NOT_CONVERGED, "wall-time cap reached (residual %g)", (double)r);
+        break;
+      }
+    }
+  }
+  stats.t = dt * (double)stats.steps;
+  stats.wall_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (s) *s = stats;
+  return rc;
+}
+
+hj_status hj_prolong(hj_grid coarse, hj_grid fine) {
+  if (!coarse || !fine) return fail(HJ_ERR_ARG, "grid is NULL");
+  if (coarse->ndim != fine->ndim) return fail(HJ_ERR_ARG, "grids differ in ndim");
+  if (coarse->device != fine->device) return fail(HJ_ERR_ARG, "grids on different devices");
+  if (!coarse->has_value) return fail(HJ_ERR_STATE, "coarse grid holds no value");
+  if (fine->con_kind < 0) return fail(HJ_ERR_STATE, "fine grid has no constraint");
+  for (int i = 0; i < fine->ndim; ++i) {
+    double tol = 1e-9 * coarse->h[i];
+    if (fine->lo[i] < coarse->lo[i] - tol || fine->hi[i] > coarse->hi[i] + tol)
+      return fail(HJ_ERR_ARG, "fine box leaves the coarse box on axis %d", i);
+  }
+  DeviceGuard dg(fine->device);
+  cudaEvent_t ev;
+  HJ_CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  cudaEventRecord(ev, coarse->stream);
+  cudaStreamWaitEvent(fine->stream, ev, 0);
+  cudaEventDestroy(ev);
+  HJ_CU(cudaMemsetAsync(fine->dscal + 5, 0, sizeof(unsigned), fine->stream));
+  HJ_CU(hjk::launch_prolong(devgrid(coarse), coarse->W, devgrid(fine), fine->W,
+                            (int*)(fine->dscal + 5), fine->stream));
+  HJ_CU(cudaMemcpyAsync(fine->hscal + 5, fine->dscal + 5, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                        fine->stream));
+  HJ_CU(cudaStreamSynchronize(fine->stream));
+  if (fine->hscal[5]) return fail(HJ_ERR_ARG, "a fine node lies outside the coarse grid");
+  fine->has_value = true;
+  return HJ_OK;
+}
+
+hj_status hj_set_value(hj_grid g, const float* src, int on_device) {
+  if (!g || !src) return fail(HJ_ERR_ARG, "NULL argument");
+  DeviceGuard dg(g->device);
+  HJ_CU(cudaMemcpyAsync(g->W, src, (size_t)g->npts * sizeof(float),
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->stream));
+  HJ_CU(cudaStreamSynchronize(g->stream));
+  g->has_value = true;
+  return HJ_OK;
+}
+
+hj_status hj_get_value(hj_grid g, float* dst, int on_device) {
+  if (!g || !dst) return fail(HJ_ERR_ARG, "NULL argument");
+  if (!g->has_value) return fail(HJ_ERR_STATE, "grid holds no value yet");
+  DeviceGuard dg(g->device);
+  HJ_CU(cudaMemcpyAsync(dst, g->W, (size_t)g->npts * sizeof(float),
+                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->stream));
+  HJ_CU(cudaStreamSynchronize(g->stream));
+  return HJ_OK;
+}
+
+static hj_status query(hj_grid g, int npts, const double* x, double* out, int grad) {
+  if (!g || npts < 0 || (npts > 0 && (!x || !out))) return fail(HJ_ERR_ARG, "bad query arguments");
+  if (!g->has_value) return fail(HJ_ERR_STATE, "grid holds no value yet");
+  if (npts == 0) return HJ_OK;
+  DeviceGuard dg(g->device);
+  size_t nin = (size_t)npts * g->ndim;
+  size_t nout = grad ? nin : (size_t)npts;
+  size_t need = nin + nout;
+  if (need > g->qcap) {
+    cudaFree(g->qbuf);
+    g->qbuf = nullptr;
+    g->qcap = 0;
+    HJ_CU(cudaMalloc(&g->qbuf, need * sizeof(double)));
+    g->qcap = need;
+  }
+  HJ_CU(cudaMemsetAsync(g->dscal + 5, 0, sizeof(unsigned), g->stream));
+  HJ_CU(cudaMemcpyAsync(g->qbuf, x, nin * sizeof(double), cudaMemcpyHostToDevice, g->stream));
+  HJ_CU(hjk::launch_query(devgrid(g), g->W, npts, g->qbuf, g->qbuf + nin, (int*)(g->dscal + 5),
+                          grad, g->stream));
+  HJ_CU(cudaMemcpyAsync(out, g->qbuf + nin, nout * sizeof(double), cudaMemcpyDeviceToHost,
+                        g->stream));
+  HJ_CU(cudaMemcpyAsync(g->hscal + 5, g->dscal + 5, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                        g->stream));
+  HJ_CU(cudaStreamSynchronize(g->stream));
+  if (g->hscal[5]) return fail(HJ_ERR_ARG, "query point outside the grid box");
+  return HJ_OK;
+}
+
+hj_status hj_query_value(hj_grid g, int npts, const double* x, double* v_out) {
+  return query(g, npts, x, v_out, 0);
+}
+
+hj_status hj_query_gradient(hj_grid g, int npts, const double* x, double* grad_out) {
+  return query(g, npts, x, grad_out, 1);
+}
+
+}  // extern "C"

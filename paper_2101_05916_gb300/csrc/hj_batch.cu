@@ -1,0 +1,428 @@
+// hj_batch.cu -- decomposed subsystems stepped together (Sec. III-A: the
+// x, y and z blocks of the 10-D quadcopter are independent problems, and the
+// paper runs them in parallel).
+//
+// Each TVD-RK3 stage of every active grid is ONE launch: a block first finds
+// its grid (binary search over block offsets), copies that grid's descriptor
+// into shared memory, and then runs the same per-node stage code as the
+// single-grid kernel.  After stage 3, a one-block control kernel advances
+// every grid's step counter.  It also closes check windows (residual vs.
+// tol) and clears the `active` flag of grids that converged, hit their cap or
+// went non-finite.  So all stop decisions happen on the device, and a round
+// of steps is a fixed launch sequence that is captured once as a CUDA graph
+// and replayed.  Blocks of inactive grids return at once; the host compacts
+// the launch at the next round boundary.
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <cstring>
+
+#include "hj_batch.h"
+#include "hj_stage.cuh"
+
+namespace hjb {
+
+constexpr int kThreads = hjk::kStageThreads;
+
+__host__ __device__ constexpr int kind_code(int model, int ndim, int scheme) {
+  return model * 100 + ndim * 10 + scheme;
+}
+
+template <int STAGE>
+__device__ __forceinline__ unsigned dispatch(const Item& it, int q, int yb, int zb, bool check) {
+  const hjd::DevGrid& g = it.g;
+  const hjd::StageArgs& a = it.a[STAGE - 1];
+  using namespace hjd;
+  switch (it.kind) {
+    case kind_code(M_QUAD_Z, 2, 1): return stage_point<2, 1, M_QUAD_Z, STAGE>(g, a, q, yb, zb, check);
+    case kind_code(M_QUAD_Z, 2, 2): return stage_point<2, 2, M_QUAD_Z, STAGE>(g, a, q, yb, zb, check);
+    case kind_code(M_QUAD_Z, 2, 5): return stage_point<2, 5, M_QUAD_Z, STAGE>(g, a, q, yb, zb, check);
+    case kind_code(M_QUAD_X4, 4, 1): return stage_point<4, 1, M_QUAD_X4, STAGE>(g, a, q, yb, zb, check);
+    case kind_code(M_QUAD_X4, 4, 2): return stage_point<4, 2, M_QUAD_X4, STAGE>(g, a, q, yb, zb, check);
+    case kind_code(M_QUAD_X4, 4, 5): return stage_point<4, 5, M_QUAD_X4, STAGE>(g, a, q, yb, zb, check);
+    case kind_code(M_DRIFT, 1, 2): return stage_point<1, 2, M_DRIFT, STAGE>(g, a, q, yb, zb, check);
+    case kind_code(M_DRIFT, 1, 5): return stage_point<1, 5, M_DRIFT, STAGE>(g, a, q, yb, zb, check);
+    case kind_code(M_DRIFT, 2, 2): return stage_point<2, 2, M_DRIFT, STAGE>(g, a, q, yb, zb, check);
+    case kind_code(M_DRIFT, 2, 5): return stage_point<2, 5, M_DRIFT, STAGE>(g, a, q, yb, zb, check);
+    default: return 0u;
+  }
+}
+
+static bool batch_supported(int model, int ndim, int scheme) {
+  if (model == hjd::M_QUAD_Z) return ndim == 2;
+  if (model == hjd::M_QUAD_X4) return ndim == 4;
+  if (model == hjd::M_DRIFT) return (ndim == 1 || ndim == 2) && (scheme == 2 || scheme == 5);
+  return false;
+}
+
+template <int STAGE>
+__global__ void __launch_bounds__(kThreads) batch_stage(const Item* __restrict__ items, int nitems,
+                                                         Ctl* ctl) {
+  __shared__ Item it;
+  __shared__ int k_s;
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = nitems - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (items[mid].block_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    k_s = lo;
+  }
+  __syncthreads();
+  {
+    const int* src = reinterpret_cast<const int*>(items + k_s);
+    int* dst = reinterpret_cast<int*>(&it);
+    for (int i = threadIdx.x; i < (int)(sizeof(Item) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  const Ctl& c = ctl[it.slot];
+  if (!c.active) return;  // uniform: written only by the control kernel
+  int lb = blockIdx.x - it.block_begin;
+  int bxi = lb % it.bx;
+  int rest = lb / it.bx;
+  int yb = rest % it.by;
+  int zb = rest / it.by;
+  bool check = false;
+  if (STAGE == 3) {
+    long long s1 = c.steps + 1;
+    check = (s1 % c.per == 0) || (s1 >= c.max_steps);
+  }
+  unsigned r = dispatch<STAGE>(it, bxi * kThreads + threadIdx.x, yb, zb, check);
+  if (STAGE == 3 && check) hjd::block_max_bits(r, &ctl[it.slot].resid);
+}
+
+__global__ void batch_control(const Item* __restrict__ items, int nitems, Ctl* ctl) {
+  for (int k = threadIdx.x; k < nitems; k += blockDim.x) {
+    Ctl& c = ctl[items[k].slot];
+    if (!c.active) continue;
+    long long s = ++c.steps;
+    if (s % c.per == 0 || s >= c.max_steps) {
+      float r = __uint_as_float(c.resid);
+      c.resid = 0u;
+      c.last_resid = r;
+      c.windows += 1;
+      if (!(r <= FLT_MAX)) {
+        c.status = S_NONFINITE;
+        c.active = 0;
+      } else if ((double)r < c.tol) {
+        c.status = S_CONVERGED;
+        c.active = 0;
+      } else if (s >= c.max_steps) {
+        c.status = S_CAP;
+        c.active = 0;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ host
+
+Runner::Runner(int device, cudaStream_t stream, int capacity)
+    : device_(device), stream_(stream), cap_(capacity), slots_(capacity) {}
+
+Runner::~Runner() {
+  hja::DeviceGuard dg(device_);
+  cudaStreamSynchronize(stream_);
+  drop_graphs();
+  cudaFree(dev_ctl_);
+  cudaFree(dev_items_);
+  if (host_ctl_) cudaFreeHost(host_ctl_);
+  if (cap_stream_) cudaStreamDestroy(cap_stream_);
+}
+
+hj_status Runner::init() {
+  hja::DeviceGuard dg(device_);
+  HJ_CU(cudaMalloc(&dev_ctl_, sizeof(Ctl) * cap_));
+  HJ_CU(cudaMallocHost(&host_ctl_, sizeof(Ctl) * cap_));
+  std::memset(host_ctl_, 0, sizeof(Ctl) * cap_);
+  HJ_CU(cudaMemsetAsync(dev_ctl_, 0, sizeof(Ctl) * cap_, stream_));
+  HJ_CU(cudaStreamCreateWithFlags(&cap_stream_, cudaStreamNonBlocking));
+  return HJ_OK;
+}
+
+void Runner::drop_graphs() {
+  for (auto& kv : graphs_) cudaGraphExecDestroy(kv.second);
+  graphs_.clear();
+}
+
+int Runner::active() const {
+  int n = 0;
+  for (int i = 0; i < cap_; ++i)
+    if (slots_[i].used && !slots_[i].done) ++n;
+  return n;
+}
+
+hj_status Runner::add(hj_grid g, int mode, const hj_solve_opts& o, int* slot_out) {
+  if (!g) return hja::fail(HJ_ERR_ARG, "grid is NULL");
+  if (g->device != device_) return hja::fail(HJ_ERR_ARG, "batch grids must share one device");
+  if (mode != HJ_COLD && mode != HJ_WARM) return hja::fail(HJ_ERR_ARG, "bad mode");
+  if (!(o.cfl > 0.0) || !(o.tol >= 0.0) || !(o.check_dt > 0.0) || o.dt < 0.0)
+    return hja::fail(HJ_ERR_ARG, "bad solve options");
+  hj_status st = hja::validate_ready(g, o.scheme);
+  if (st != HJ_OK) return st;
+  if (!batch_supported(g->model, g->ndim, o.scheme))
+    return hja::fail(HJ_ERR_ARG, "model %d, %d-D, scheme %d has no batched kernel", g->model,
+                     g->ndim, o.scheme);
+  if (mode == HJ_WARM && !g->has_value) return hja::fail(HJ_ERR_STATE, "warm start without prior");
+  for (int i = 0; i < cap_; ++i)
+    if (slots_[i].used && !slots_[i].done && slots_[i].g == g)
+      return hja::fail(HJ_ERR_ARG, "grid already stepping in this batch");
+  int k = -1;
+  for (int i = 0; i < cap_; ++i)
+    if (!slots_[i].used) {
+      k = i;
+      break;
+    }
+  if (k < 0) return hja::fail(HJ_ERR_OOM, "batch is full (%d grids)", cap_);
+  hja::DeviceGuard dg(device_);
+  if ((st = hja::ensure_alpha(g)) != HJ_OK) return st;
+  double dt = o.dt > 0.0 ? o.dt : hja::cfl_dt(g, o.cfl);
+  // order the grid's own stream before the batch stream
+  if (g->stream != stream_) HJ_CU(cudaStreamSynchronize(g->stream));
+  hjd::DevGrid d = hja::devgrid(g);
+  HJ_CU(hjk::launch_init(d, g->W, g->snap, mode == HJ_WARM ? 1 : 0, stream_));
+  g->has_value = true;
+  Slot& s = slots_[k];
+  s = Slot();
+  s.g = g;
+  s.used = true;
+  s.scheme = o.scheme;
+  s.clamp = o.clamp;
+  s.dt = dt;
+  s.max_wall_ms = o.max_wall_ms;
+  s.t0 = std::chrono::steady_clock::now();
+  Ctl c;
+  std::memset(&c, 0, sizeof(c));
+  c.active = dt > 0.0 ? 1 : 0;
+  c.status = dt > 0.0 ? S_RUNNING : S_CONVERGED;
+  if (o.fixed_steps > 0) {
+    s.fixed = true;
+    c.per = o.fixed_steps;
+    c.max_steps = o.fixed_steps;
+    c.tol = -1.0;
+  } else {
+    long long per = (long long)std::ceil(o.check_dt / std::max(dt, 1e-300) - 1e-9);
+    c.per = std::max(per, 1ll);
+    c.max_steps = o.max_steps > 0 ? o.max_steps : (1ll << 62);
+    c.tol = o.tol;
+  }
+  host_ctl_[k] = c;
+  HJ_CU(cudaMemcpyAsync(dev_ctl_ + k, &host_ctl_[k], sizeof(Ctl), cudaMemcpyHostToDevice, stream_));
+  HJ_CU(cudaStreamSynchronize(stream_));
+  if (!c.active) {
+    s.done = true;
+  }
+  dirty_ = true;
+  if (slot_out) *slot_out = k;
+  return HJ_OK;
+}
+
+hj_status Runner::cancel(int k) {
+  if (k < 0 || k >= cap_ || !slots_[k].used) return hja::fail(HJ_ERR_ARG, "bad slot");
+  if (slots_[k].done) return HJ_OK;
+  hja::DeviceGuard dg(device_);
+  // written between rounds only, so no kernel of this runner reads it concurrently
+  HJ_CU(cudaStreamSynchronize(stream_));
+  host_ctl_[k].active = 0;
+  host_ctl_[k].status = S_CANCELLED;
+  HJ_CU(cudaMemcpyAsync(dev_ctl_ + k, &host_ctl_[k], sizeof(Ctl), cudaMemcpyHostToDevice, stream_));
+  HJ_CU(cudaStreamSynchronize(stream_));
+  slots_[k].done = true;
+  slots_[k].wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() -
+                                                                slots_[k].t0).count();
+  dirty_ = true;
+  return HJ_OK;
+}
+
+hj_status Runner::rebuild() {
+  std::vector<Item> items;
+  order_.clear();
+  int begin = 0;
+  for (int k = 0; k < cap_; ++k) {
+    Slot& s = slots_[k];
+    if (!s.used || s.done) continue;
+    hj_grid g = s.g;
+    Item it;
+    std::memset(&it, 0, sizeof(it));
+    it.g = hja::devgrid(g);
+    float dt = (float)s.dt;
+    it.a[0] = hjd::StageArgs{g->W, g->W, g->A, nullptr, nullptr, dt, 0, s.clamp};
+    it.a[1] = hjd::StageArgs{g->A, g->W, g->B, nullptr, nullptr, dt, 0, s.clamp};
+    it.a[2] = hjd::StageArgs{g->B, g->W, g->W, g->snap, nullptr, dt, 1, s.clamp};
+    it.kind = kind_code(g->model, g->ndim, s.scheme);
+    it.slot = k;
+    it.bx = (it.g.plane + kThreads - 1) / kThreads;
+    it.by = g->ndim >= 3 ? g->n[g->ndim - 3] : 1;
+    int bz = g->ndim == 4 ? g->n[0] : 1;
+    it.block_begin = begin;
+    begin += it.bx * it.by * bz;
+    items.push_back(it);
+    order_.push_back(k);
+  }
+  nitems_ = (int)items.size();
+  total_blocks_ = begin;
+  if (nitems_ > item_cap_) {
+    cudaFree(dev_items_);
+    dev_items_ = nullptr;
+    item_cap_ = std::max(nitems_, 2 * item_cap_);
+    HJ_CU(cudaMalloc(&dev_items_, sizeof(Item) * item_cap_));
+  }
+  if (nitems_) {
+    HJ_CU(cudaMemcpyAsync(dev_items_, items.data(), sizeof(Item) * nitems_, cudaMemcpyHostToDevice,
+                          stream_));
+    HJ_CU(cudaStreamSynchronize(stream_));
+  }
+  drop_graphs();
+  dirty_ = false;
+  return HJ_OK;
+}
+
+static cudaError_t enqueue_round(const Item* items, int nitems, int blocks, Ctl* ctl, long long R,
+                                 cudaStream_t s) {
+  for (long long i = 0; i < R; ++i) {
+    batch_stage<1><<<blocks, kThreads, 0, s>>>(items, nitems, ctl);
+    batch_stage<2><<<blocks, kThreads, 0, s>>>(items, nitems, ctl);
+    batch_stage<3><<<blocks, kThreads, 0, s>>>(items, nitems, ctl);
+    batch_control<<<1, 256, 0, s>>>(items, nitems, ctl);
+  }
+  return cudaGetLastError();
+}
+
+hj_status Runner::sync_ctl() {
+  HJ_CU(cudaMemcpyAsync(host_ctl_, dev_ctl_, sizeof(Ctl) * cap_, cudaMemcpyDeviceToHost, stream_));
+  HJ_CU(cudaStreamSynchronize(stream_));
+  auto now = std::chrono::steady_clock::now();
+  for (int k : order_) {
+    Slot& s = slots_[k];
+    if (s.done) continue;
+    if (!host_ctl_[k].active) {
+      s.done = true;
+      s.wall_ms = std::chrono::duration<double, std::milli>(now - s.t0).count();
+      dirty_ = true;
+    }
+  }
+  return HJ_OK;
+}
+
+hj_status Runner::round(bool use_graph) {
+  hja::DeviceGuard dg(device_);
+  hj_status st;
+  if (dirty_ && (st = rebuild()) != HJ_OK) return st;
+  if (nitems_ == 0) return HJ_OK;
+  // run to the next window boundary of any active grid
+  long long R = 1ll << 62;
+  for (int k : order_) {
+    const Ctl& c = host_ctl_[k];
+    long long to_window = c.per - (c.steps % c.per);
+    long long to_cap = c.max_steps - c.steps;
+    R = std::min(R, std::min(to_window, to_cap));
+  }
+  R = std::max(1ll, std::min(R, 4096ll));
+  if (use_graph) {
+    auto it = graphs_.find(R);
+    if (it == graphs_.end()) {
+      cudaGraph_t graph = nullptr;
+      HJ_CU(cudaStreamBeginCapture(cap_stream_, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = enqueue_round(dev_items_, nitems_, total_blocks_, dev_ctl_, R, cap_stream_);
+      cudaError_t e2 = cudaStreamEndCapture(cap_stream_, &graph);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return hja::fail(HJ_ERR_CUDA, "batch capture: %s",
+                         cudaGetErrorString(e != cudaSuccess ? e : e2));
+      }
+      cudaGraphExec_t ex = nullptr;
+      cudaError_t e3 = cudaGraphInstantiate(&ex, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e3 != cudaSuccess) return hja::fail(HJ_ERR_CUDA, "batch instantiate: %s", cudaGetErrorString(e3));
+      it = graphs_.emplace(R, ex).first;
+    }
+    HJ_CU(cudaGraphLaunch(it->second, stream_));
+  } else {
+    HJ_CU(enqueue_round(dev_items_, nitems_, total_blocks_, dev_ctl_, R, stream_));
+  }
+  hjk::g_launches.fetch_add(4ull * (unsigned long long)R);
+  if ((st = sync_ctl()) != HJ_OK) return st;
+  // wall-time caps are host-side and apply between rounds
+  auto now = std::chrono::steady_clock::now();
+  for (int k : order_) {
+    Slot& s = slots_[k];
+    if (s.done || s.max_wall_ms <= 0.0) continue;
+    double ms = std::chrono::duration<double, std::milli>(now - s.t0).count();
+    if (ms > s.max_wall_ms) {
+      if ((st = cancel(k)) != HJ_OK) return st;
+      s.wall_capped = true;
+    }
+  }
+  return HJ_OK;
+}
+
+hj_status Runner::collect(int k, hj_solve_stats* out) {
+  if (k < 0 || k >= cap_ || !slots_[k].used || !slots_[k].done)
+    return hja::fail(HJ_ERR_ARG, "slot not finished");
+  Slot& s = slots_[k];
+  const Ctl& c = host_ctl_[k];
+  hj_solve_stats st;
+  std::memset(&st, 0, sizeof(st));
+  st.steps = c.steps;
+  st.dt = s.dt;
+  st.t = s.dt * (double)c.steps;
+  st.residual = c.last_resid;
+  st.windows = c.windows;
+  st.wall_ms = s.wall_ms;
+  st.converged = c.status == S_CONVERGED;
+  hj_status rc = HJ_OK;
+  if (s.fixed) {
+    st.converged = 0;
+    if (c.status == S_NONFINITE) rc = hja::fail(HJ_ERR_DIVERGED, "non-finite value");
+  } else if (c.status == S_NONFINITE) {
+    rc = hja::fail(HJ_ERR_DIVERGED, "non-finite value after %lld steps", c.steps);
+  } else if (c.status == S_CAP || s.wall_capped) {
+    rc = hja::fail(HJ_ERR_NOT_CONVERGED, "step or time cap reached (residual %g)", (double)c.last_resid);
+  } else if (c.status == S_CANCELLED) {
+    rc = hja::fail(HJ_ERR_ABORTED, "cancelled");
+  }
+  if (out) *out = st;
+  s = Slot();
+  return rc;
+}
+
+}  // namespace hjb
+
+extern "C" hj_status hj_solve_batch(hj_grid* gs, int ngrids, const int* modes,
+                                    const hj_solve_opts* opts, int opts_count,
+                                    hj_solve_stats* stats, int* status_out) {
+  if (!gs || ngrids < 1 || !modes) return hja::fail(HJ_ERR_ARG, "bad batch arguments");
+  if (opts && opts_count != 1 && opts_count != ngrids)
+    return hja::fail(HJ_ERR_ARG, "opts_count must be 1 or ngrids");
+  for (int i = 0; i < ngrids; ++i) {
+    if (!gs[i]) return hja::fail(HJ_ERR_ARG, "grid %d is NULL", i);
+    for (int j = 0; j < i; ++j)
+      if (gs[j] == gs[i]) return hja::fail(HJ_ERR_ARG, "grid %d appears twice", i);
+  }
+  hjb::Runner r(gs[0]->device, gs[0]->stream, std::max(ngrids, 1));
+  hj_status st = r.init();
+  if (st != HJ_OK) return st;
+  std::vector<int> slot(ngrids, -1);
+  bool graph = true;
+  for (int i = 0; i < ngrids; ++i) {
+    hj_solve_opts o;
+    hj_default_opts(&o);
+    if (opts) o = opts[opts_count == 1 ? 0 : i];
+    graph = graph && o.use_graph;
+    st = r.add(gs[i], modes[i], o, &slot[i]);
+    if (st != HJ_OK) return st;
+  }
+  while (r.active() > 0) {
+    st = r.round(graph);
+    if (st != HJ_OK) return st;
+  }
+  hj_status first = HJ_OK;
+  for (int i = 0; i < ngrids; ++i) {
+    hj_solve_stats s;
+    hj_status si = r.collect(slot[i], &s);
+    if (stats) stats[i] = s;
+    if (status_out) status_out[i] = si;
+    if (first == HJ_OK && si != HJ_OK) first = si;
+  }
+  return first;
+}

@@ -1,0 +1,87 @@
+// hj_batch.h -- fused multi-grid stepping shared by hj_solve_batch and the server.
+#pragma once
+
+#include <chrono>
+#include <map>
+#include <vector>
+
+#include "hj_grid.h"
+
+namespace hjb {
+
+// One grid inside a fused launch (device memory; copied to shared memory per block).
+struct Item {
+  hjd::DevGrid g;
+  hjd::StageArgs a[3];  // stage 1..3 arguments (check is decided on the device)
+  int kind;             // model * 100 + ndim * 10 + scheme
+  int slot;             // index into the control array
+  int block_begin;      // first block of this grid in the fused launch
+  int bx, by;           // plane blocks; slabs along axis ndim-3
+};
+
+// Per-grid stepping state, written only by the control kernel between steps.
+struct Ctl {
+  int active;         // 1 while the grid is stepping
+  int status;         // 0 running, 1 converged, 2 step cap, 3 non-finite, 4 cancelled
+  long long per;      // steps per check window
+  long long steps;    // steps done
+  long long max_steps;
+  long long windows;
+  double tol;         // stop when the window residual drops below (negative: never)
+  unsigned resid;     // running window residual (float bits)
+  float last_resid;
+};
+
+enum { S_RUNNING = 0, S_CONVERGED = 1, S_CAP = 2, S_NONFINITE = 3, S_CANCELLED = 4 };
+
+// Steps a changing set of grids together.  Grids join with add() and leave
+// when their control state says so; every round advances all active grids by
+// the same number of steps in one fused launch per RK stage.
+class Runner {
+ public:
+  Runner(int device, cudaStream_t stream, int capacity = 1024);
+  ~Runner();
+  hj_status init();
+  // Validate, run the init kernel and set up the control slot.  Returns the slot.
+  hj_status add(hj_grid g, int mode, const hj_solve_opts& o, int* slot);
+  // Advance every active grid until the next window boundary of any of them.
+  hj_status round(bool use_graph);
+  // Ask an active slot to stop at the next round boundary.
+  hj_status cancel(int slot);
+  int active() const;
+  bool finished(int slot) const { return slots_[slot].done; }
+  // Final state of a finished slot; frees the slot for reuse.
+  hj_status collect(int slot, hj_solve_stats* st);
+  long long steps_of(int slot) const { return host_ctl_[slot].steps; }
+  cudaStream_t stream() const { return stream_; }
+
+ private:
+  struct Slot {
+    hj_grid g = nullptr;
+    bool used = false, done = false, fixed = false, wall_capped = false;
+    int scheme = 5, clamp = 0;
+    double dt = 0.0, max_wall_ms = 0.0;
+    std::chrono::steady_clock::time_point t0;
+    double wall_ms = 0.0;
+  };
+  hj_status rebuild();
+  hj_status sync_ctl();
+  void drop_graphs();
+
+  int device_;
+  cudaStream_t stream_;
+  int cap_;
+  std::vector<Slot> slots_;
+  Ctl* dev_ctl_ = nullptr;
+  Ctl* host_ctl_ = nullptr;  // pinned mirror
+  Item* dev_items_ = nullptr;
+  int item_cap_ = 0;
+  int nitems_ = 0;
+  int total_blocks_ = 0;
+  bool dirty_ = true;
+  std::vector<int> order_;  // slots in the current item list
+  std::map<long long, cudaGraphExec_t> graphs_;  // round length -> graph
+  cudaStream_t cap_stream_ = nullptr;
+};
+
+}  // namespace hjb

@@ -1,0 +1,76 @@
+// hj_grid.h -- the grid handle shared by the C ABI translation units.
+#pragma once
+
+#include <cstdarg>
+#include <cuda_runtime.h>
+
+#include "hj.h"
+#include "hj_internal.h"
+
+struct hj_grid_s {
+  int device = 0;
+  int ndim = 0;
+  int n[HJ_MAX_DIM] = {0, 0, 0, 0};
+  double lo[HJ_MAX_DIM] = {0, 0, 0, 0};
+  double hi[HJ_MAX_DIM] = {0, 0, 0, 0};
+  double h[HJ_MAX_DIM] = {0, 0, 0, 0};
+  long long npts = 0;
+  cudaStream_t stream = nullptr;      // caller's stream (nullptr = legacy default)
+  cudaStream_t cap_stream = nullptr;  // private stream used only for graph capture
+
+  int model = -1;
+  double params[8] = {0};
+  int nd = 0;
+  double d_lo[HJ_MAX_DIM] = {0}, d_hi[HJ_MAX_DIM] = {0};
+  int con_kind = -1;
+  double ca[HJ_MAX_DIM] = {0}, cb[HJ_MAX_DIM] = {0};
+
+  float* W = nullptr;      // value function (result, or prior for a warm start)
+  float* A = nullptr;      // RK stage 1
+  float* B = nullptr;      // RK stage 2
+  float* snap = nullptr;   // W at the start of the current check window
+  float* tab = nullptr;    // per-index coefficient table of the model
+  unsigned* dscal = nullptr;  // device scalars: [0..3] alpha bits, [4] residual bits, [5] flag
+  unsigned* hscal = nullptr;  // pinned host mirror of dscal
+  double* qbuf = nullptr;     // query staging (device)
+  size_t qcap = 0;
+
+  bool has_value = false;
+  bool alpha_valid = false;
+  float alpha[HJ_MAX_DIM] = {0, 0, 0, 0};
+
+  cudaGraphExec_t gexec = nullptr;  // cached graph of one check window
+  long long g_per = 0;
+  float g_dt = 0.f;
+  int g_scheme = 0, g_clamp = 0;
+};
+
+namespace hja {
+
+hj_status fail(hj_status s, const char* fmt, ...);
+hjd::DevGrid devgrid(const hj_grid g);
+hj_status ensure_alpha(hj_grid g);
+hj_status validate_ready(hj_grid g, int scheme);
+double cfl_dt(const hj_grid g, double cfl);
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace hja
+
+#define HJ_CU(call)                                                                         \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return hja::fail(e_ == cudaErrorMemoryAllocation ? HJ_ERR_OOM : HJ_ERR_CUDA,          \
+                       "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)

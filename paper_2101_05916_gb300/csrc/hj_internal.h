@@ -1,0 +1,39 @@
+// hj_internal.h -- host-side launch interface between the C ABI layer and the
+// kernels.  Not installed; not part of the public ABI.
+#pragma once
+
+#include <atomic>
+#include <cuda_runtime.h>
+
+#include "hj_device.cuh"
+
+namespace hjk {
+
+// kernels launched by this library so far (graph replays count every kernel node)
+extern std::atomic<unsigned long long> g_launches;
+
+// Threads per block of the stencil kernels.
+constexpr int kStageThreads = 256;
+
+// One TVD-RK3 stage on one grid.  stage is 1, 2 or 3; scheme 1, 2 or 5.
+cudaError_t launch_stage(const hjd::DevGrid& g, int scheme, int stage, const hjd::StageArgs& a,
+                         cudaStream_t s);
+// Per-axis max |f_i| over grid nodes and input vertices, as float bits into out[0..ndim).
+// out must be zeroed first.
+cudaError_t launch_alpha(const hjd::DevGrid& g, unsigned* out, cudaStream_t s);
+// W = l (warm = 0) or W = min(W, l) (warm = 1); snap = W.
+cudaError_t launch_init(const hjd::DevGrid& g, float* W, float* snap, int warm, cudaStream_t s);
+// Wf = min(multilinear(Wc) at fine nodes, l_fine); *bad = 1 if a fine node lies
+// outside the coarse box.
+cudaError_t launch_prolong(const hjd::DevGrid& c, const float* Wc, const hjd::DevGrid& f,
+                           float* Wf, int* bad, cudaStream_t s);
+// Multilinear value (grad = 0) or node-gradient interpolation (grad = 1) at npts
+// points x (device, point-major doubles).  *bad is set to 1 when a point lies
+// outside the box.
+cudaError_t launch_query(const hjd::DevGrid& g, const float* W, int npts, const double* x,
+                         double* out, int* bad, int grad, cudaStream_t s);
+
+// Whether (model, ndim, scheme) has a compiled stencil.
+bool stage_supported(int model, int ndim, int scheme);
+
+}  // namespace hjk

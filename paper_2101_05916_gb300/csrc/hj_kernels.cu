@@ -1,0 +1,311 @@
+// hj_kernels.cu -- sm_103a kernels of the HJ level-set solve.
+//
+//  stage_kernel   one TVD-RK3 stage: slopes on every axis, Lax-Friedrichs
+//                 Hamiltonian, the RK combination, and in stage 3 the clamp
+//                 W <- min(W3, l) of Eq. 2 plus the window residual.
+//  alpha_kernel   max-reduction of |f_i| over the grid for the LF
+//                 coefficients and the CFL dt.
+//  init_kernel    cold start W = l, or warm start W = min(prior, l) (Sec. III-B).
+//  prolong_kernel coarse-to-fine migration (Sec. III-C).
+//  query_kernel   value / gradient read-out for the safety controller (Sec. II-A).
+//
+// The stencil is FP32-issue bound (about 500 FP32 instructions per node and
+// stage for WENO5 in 4-D against 8-12 bytes of compulsory traffic), so
+// threads map one-to-one onto nodes of the flattened last-two-axes plane.
+// That keeps warps fully populated whatever the axis lengths.  Line
+// neighbours come through the read-only (L1) path; warps of a block cover
+// adjacent rows, which makes the +-3 neighbours along the two fast axes L1
+// hits.
+#include <algorithm>
+#include <cstdio>
+
+#include "hj_internal.h"
+#include "hj_stage.cuh"
+
+namespace hjk {
+
+std::atomic<unsigned long long> g_launches{0};
+
+using hjd::DevGrid;
+using hjd::StageArgs;
+
+template <int D, int S, int M, int STAGE>
+__global__ void __launch_bounds__(kStageThreads) stage_kernel(const DevGrid g, const StageArgs a) {
+  unsigned r = hjd::stage_point<D, S, M, STAGE>(g, a, blockIdx.x * blockDim.x + threadIdx.x,
+                                                blockIdx.y, blockIdx.z, a.check != 0);
+  if constexpr (STAGE == 3) {
+    if (a.check) hjd::block_max_bits(r, a.resid);
+  }
+}
+
+template <int D>
+__device__ __forceinline__ void unravel(const DevGrid& g, int pt, int (&idx)[D]) {
+#pragma unroll
+  for (int d = D - 1; d > 0; --d) {
+    int q = pt / g.n[d];
+    idx[d] = pt - q * g.n[d];
+    pt = q;
+  }
+  idx[0] = pt;
+}
+
+using hjd::coords;
+
+template <int D, int M>
+__global__ void alpha_kernel(const DevGrid g, unsigned* out) {
+  float m[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) m[d] = 0.f;
+  for (int pt = blockIdx.x * blockDim.x + threadIdx.x; pt < g.npts; pt += gridDim.x * blockDim.x) {
+    int idx[D];
+    float x[D];
+    unravel<D>(g, pt, idx);
+    coords<D>(g, idx, x);
+    hjd::abs_f_max<M, D>(g, x, idx, m);
+  }
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    hjd::block_max_bits(__float_as_uint(m[d]), out + d);
+    __syncthreads();
+  }
+}
+
+template <int D>
+__global__ void init_kernel(const DevGrid g, float* W, float* snap, int warm) {
+  for (int pt = blockIdx.x * blockDim.x + threadIdx.x; pt < g.npts; pt += gridDim.x * blockDim.x) {
+    int idx[D];
+    float x[D];
+    unravel<D>(g, pt, idx);
+    coords<D>(g, idx, x);
+    float l = hjd::margin<D>(g, x);
+    float w = warm ? fminf(W[pt], l) : l;
+    W[pt] = w;
+    snap[pt] = w;
+  }
+}
+
+// Coarse cell and fractional offset of coordinate xv along axis d of grid c.
+__device__ __forceinline__ bool locate(const DevGrid& c, int d, double xv, int& i0, double& fr) {
+  double t = (xv - c.lo_d[d]) / c.h_d[d];
+  double tol = 1e-9;
+  if (t < -tol || t > (double)(c.n[d] - 1) + tol) return false;
+  int i = (int)floor(t);
+  i = min(max(i, 0), c.n[d] - 2);
+  double f = t - (double)i;
+  fr = fmin(fmax(f, 0.0), 1.0);
+  i0 = i;
+  return true;
+}
+
+template <int D>
+__global__ void prolong_kernel(const DevGrid c, const float* __restrict__ Wc, const DevGrid f,
+                               float* Wf, int* bad) {
+  for (int pt = blockIdx.x * blockDim.x + threadIdx.x; pt < f.npts; pt += gridDim.x * blockDim.x) {
+    int idx[D];
+    unravel<D>(f, pt, idx);
+    int i0[D];
+    double fr[D];
+    float xf[D];
+    bool ok = true;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      double xv = f.lo_d[d] + (double)idx[d] * f.h_d[d];
+      xf[d] = (float)xv;
+      ok = ok && locate(c, d, xv, i0[d], fr[d]);
+    }
+    if (!ok) {
+      *bad = 1;
+      continue;
+    }
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < (1 << D); ++k) {
+      double wgt = 1.0;
+      int off = 0;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        int bit = (k >> d) & 1;
+        wgt *= bit ? fr[d] : 1.0 - fr[d];
+        off += (i0[d] + bit) * c.stride[d];
+      }
+      acc += wgt * (double)__ldg(Wc + off);
+    }
+    Wf[pt] = fminf((float)acc, hjd::margin<D>(f, xf));
+  }
+}
+
+// Node gradient along axis d: central difference, one-sided at the ends.
+template <int D>
+__device__ __forceinline__ double node_grad(const DevGrid& g, const float* W, int off, int i, int d) {
+  int s = g.stride[d];
+  if (i == 0) return ((double)W[off + s] - (double)W[off]) / g.h_d[d];
+  if (i == g.n[d] - 1) return ((double)W[off] - (double)W[off - s]) / g.h_d[d];
+  return ((double)W[off + s] - (double)W[off - s]) / (2.0 * g.h_d[d]);
+}
+
+template <int D>
+__global__ void query_kernel(const DevGrid g, const float* __restrict__ W, int npts,
+                             const double* __restrict__ xs, double* out, int* bad, int grad) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= npts) return;
+  int i0[D];
+  double fr[D];
+  bool ok = true;
+#pragma unroll
+  for (int d = 0; d < D; ++d) ok = ok && locate(g, d, xs[k * D + d], i0[d], fr[d]);
+  if (!ok) {
+    *bad = 1;
+    return;
+  }
+  double acc[D + 1];
+#pragma unroll
+  for (int e = 0; e <= D; ++e) acc[e] = 0.0;
+#pragma unroll
+  for (int c = 0; c < (1 << D); ++c) {
+    double wgt = 1.0;
+    int off = 0;
+    int ci[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      int bit = (c >> d) & 1;
+      wgt *= bit ? fr[d] : 1.0 - fr[d];
+      ci[d] = i0[d] + bit;
+      off += ci[d] * g.stride[d];
+    }
+    if (grad) {
+#pragma unroll
+      for (int d = 0; d < D; ++d) acc[d] += wgt * node_grad<D>(g, W, off, ci[d], d);
+    } else {
+      acc[0] += wgt * (double)W[off];
+    }
+  }
+  if (grad) {
+#pragma unroll
+    for (int d = 0; d < D; ++d) out[k * D + d] = acc[d];
+  } else {
+    out[k] = acc[0];
+  }
+}
+
+// ------------------------------------------------------------- dispatch
+
+static dim3 stage_grid(const DevGrid& g) {
+  unsigned bx = (unsigned)((g.plane + kStageThreads - 1) / kStageThreads);
+  unsigned by = g.ndim >= 3 ? (unsigned)g.n[g.ndim - 3] : 1u;
+  unsigned bz = g.ndim == 4 ? (unsigned)g.n[0] : 1u;
+  return dim3(bx, by, bz);
+}
+
+template <int D, int S, int M>
+static cudaError_t stage_dispatch(const DevGrid& g, int stage, const StageArgs& a, cudaStream_t s) {
+  dim3 grid = stage_grid(g), block(kStageThreads);
+  switch (stage) {
+    case 1: stage_kernel<D, S, M, 1><<<grid, block, 0, s>>>(g, a); break;
+    case 2: stage_kernel<D, S, M, 2><<<grid, block, 0, s>>>(g, a); break;
+    default: stage_kernel<D, S, M, 3><<<grid, block, 0, s>>>(g, a); break;
+  }
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+template <int D, int M>
+static cudaError_t stage_by_scheme(const DevGrid& g, int scheme, int stage, const StageArgs& a,
+                                   cudaStream_t s) {
+  switch (scheme) {
+    case 1: return stage_dispatch<D, 1, M>(g, stage, a, s);
+    case 2: return stage_dispatch<D, 2, M>(g, stage, a, s);
+    case 5: return stage_dispatch<D, 5, M>(g, stage, a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+bool stage_supported(int model, int ndim, int scheme) {
+  if (scheme != 1 && scheme != 2 && scheme != 5) return false;
+  if (model == hjd::M_QUAD_Z) return ndim == 2;
+  if (model == hjd::M_QUAD_X4) return ndim == 4;
+  if (model == hjd::M_DRIFT) return ndim >= 1 && ndim <= 4;
+  return false;
+}
+
+cudaError_t launch_stage(const DevGrid& g, int scheme, int stage, const StageArgs& a, cudaStream_t s) {
+  switch (g.model) {
+    case hjd::M_QUAD_Z: return stage_by_scheme<2, hjd::M_QUAD_Z>(g, scheme, stage, a, s);
+    case hjd::M_QUAD_X4: return stage_by_scheme<4, hjd::M_QUAD_X4>(g, scheme, stage, a, s);
+    default:
+      switch (g.ndim) {
+        case 1: return stage_by_scheme<1, hjd::M_DRIFT>(g, scheme, stage, a, s);
+        case 2: return stage_by_scheme<2, hjd::M_DRIFT>(g, scheme, stage, a, s);
+        case 3: return stage_by_scheme<3, hjd::M_DRIFT>(g, scheme, stage, a, s);
+        case 4: return stage_by_scheme<4, hjd::M_DRIFT>(g, scheme, stage, a, s);
+      }
+  }
+  return cudaErrorInvalidValue;
+}
+
+static unsigned flat_blocks(int npts, int threads) {
+  int b = (npts + threads - 1) / threads;
+  // grid-stride loops: cap at a few waves of the 152 SMs
+  return (unsigned)std::min(b, 152 * 16);
+}
+
+cudaError_t launch_alpha(const DevGrid& g, unsigned* out, cudaStream_t s) {
+  unsigned nb = flat_blocks(g.npts, 256);
+  switch (g.model) {
+    case hjd::M_QUAD_Z: alpha_kernel<2, hjd::M_QUAD_Z><<<nb, 256, 0, s>>>(g, out); break;
+    case hjd::M_QUAD_X4: alpha_kernel<4, hjd::M_QUAD_X4><<<nb, 256, 0, s>>>(g, out); break;
+    default:
+      switch (g.ndim) {
+        case 1: alpha_kernel<1, hjd::M_DRIFT><<<nb, 256, 0, s>>>(g, out); break;
+        case 2: alpha_kernel<2, hjd::M_DRIFT><<<nb, 256, 0, s>>>(g, out); break;
+        case 3: alpha_kernel<3, hjd::M_DRIFT><<<nb, 256, 0, s>>>(g, out); break;
+        case 4: alpha_kernel<4, hjd::M_DRIFT><<<nb, 256, 0, s>>>(g, out); break;
+        default: return cudaErrorInvalidValue;
+      }
+  }
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init(const DevGrid& g, float* W, float* snap, int warm, cudaStream_t s) {
+  unsigned nb = flat_blocks(g.npts, 256);
+  switch (g.ndim) {
+    case 1: init_kernel<1><<<nb, 256, 0, s>>>(g, W, snap, warm); break;
+    case 2: init_kernel<2><<<nb, 256, 0, s>>>(g, W, snap, warm); break;
+    case 3: init_kernel<3><<<nb, 256, 0, s>>>(g, W, snap, warm); break;
+    case 4: init_kernel<4><<<nb, 256, 0, s>>>(g, W, snap, warm); break;
+    default: return cudaErrorInvalidValue;
+  }
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prolong(const DevGrid& c, const float* Wc, const DevGrid& f, float* Wf,
+                           int* bad, cudaStream_t s) {
+  unsigned nb = flat_blocks(f.npts, 256);
+  switch (f.ndim) {
+    case 1: prolong_kernel<1><<<nb, 256, 0, s>>>(c, Wc, f, Wf, bad); break;
+    case 2: prolong_kernel<2><<<nb, 256, 0, s>>>(c, Wc, f, Wf, bad); break;
+    case 3: prolong_kernel<3><<<nb, 256, 0, s>>>(c, Wc, f, Wf, bad); break;
+    case 4: prolong_kernel<4><<<nb, 256, 0, s>>>(c, Wc, f, Wf, bad); break;
+    default: return cudaErrorInvalidValue;
+  }
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_query(const DevGrid& g, const float* W, int npts, const double* x, double* out,
+                         int* bad, int grad, cudaStream_t s) {
+  unsigned nb = (unsigned)((npts + 127) / 128);
+  if (nb == 0) return cudaSuccess;
+  switch (g.ndim) {
+    case 1: query_kernel<1><<<nb, 128, 0, s>>>(g, W, npts, x, out, bad, grad); break;
+    case 2: query_kernel<2><<<nb, 128, 0, s>>>(g, W, npts, x, out, bad, grad); break;
+    case 3: query_kernel<3><<<nb, 128, 0, s>>>(g, W, npts, x, out, bad, grad); break;
+    case 4: query_kernel<4><<<nb, 128, 0, s>>>(g, W, npts, x, out, bad, grad); break;
+    default: return cudaErrorInvalidValue;
+  }
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+}  // namespace hjk

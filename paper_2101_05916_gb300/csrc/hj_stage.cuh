@@ -1,0 +1,81 @@
+// hj_stage.cuh -- one TVD-RK3 stage at one grid node, shared by the
+// single-grid kernel and the fused multi-grid (batched) kernel.
+#pragma once
+
+#include "hj_device.cuh"
+
+namespace hjd {
+
+// Node handled by plane index q in slab (yb, zb): the plane holds the last
+// two axes (all of them for ndim <= 2); yb indexes axis ndim-3 and zb axis 0
+// of a 4-D grid.
+template <int D>
+__device__ __forceinline__ bool node_of(const DevGrid& g, int q, int yb, int zb, int (&idx)[D],
+                                        int& p) {
+  if constexpr (D == 1) {
+    idx[0] = q;
+    p = q;
+    return q < g.n[0];
+  } else {
+    int inner = g.n[D - 1];
+    int a = q / inner;
+    idx[D - 2] = a;
+    idx[D - 1] = q - a * inner;
+    p = q;
+    if constexpr (D >= 3) {
+      idx[D - 3] = yb;
+      p += yb * g.stride[D - 3];
+    }
+    if constexpr (D == 4) {
+      idx[0] = zb;
+      p += zb * g.stride[0];
+    }
+    return q < g.plane;
+  }
+}
+
+template <int D>
+__device__ __forceinline__ void coords(const DevGrid& g, const int (&idx)[D], float (&x)[D]) {
+#pragma unroll
+  for (int d = 0; d < D; ++d) x[d] = fmaf((float)idx[d], g.h[d], g.lo[d]);
+}
+
+// Stage STAGE of one TVD-RK3 step at the node of (q, yb, zb):
+//   1: W1 = W + dt L(W)
+//   2: W2 = 3/4 W + 1/4 (W1 + dt L(W1))
+//   3: W3 = 1/3 W + 2/3 (W2 + dt L(W2)),  W <- min(W3, l)  [, W_prev]
+// Returns the window-residual contribution |W_new - snap| as float bits
+// (stage 3 with check; 0 otherwise).
+template <int D, int S, int M, int STAGE>
+__device__ __forceinline__ unsigned stage_point(const DevGrid& g, const StageArgs& a, int q, int yb,
+                                                int zb, bool check) {
+  int idx[D];
+  int p;
+  if (!node_of<D>(g, q, yb, zb, idx, p)) return 0u;
+  float x[D];
+  coords<D>(g, idx, x);
+  float c;
+  float L = lf_rhs<D, S, M>(g, a.src, p, idx, x, c);
+  float stepped = fmaf(a.dt, L, c);
+  if constexpr (STAGE == 1) {
+    a.dst[p] = stepped;
+    return 0u;
+  } else if constexpr (STAGE == 2) {
+    float w = a.base[p];
+    a.dst[p] = fmaf(0.75f, w, 0.25f * stepped);
+    return 0u;
+  } else {
+    float w = a.base[p];
+    float w3 = fmaf(1.f / 3.f, w, (2.f / 3.f) * stepped);
+    float wn = fminf(w3, margin<D>(g, x));
+    if (a.clamp) wn = fminf(wn, w);
+    if (w3 != w3) wn = w3;  // keep a NaN visible to the stop test
+    a.dst[p] = wn;
+    if (!check) return 0u;
+    float r = fabsf(wn - a.snap[p]);
+    a.snap[p] = wn;
+    return __float_as_uint(r);
+  }
+}
+
+}  // namespace hjd

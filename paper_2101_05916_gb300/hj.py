@@ -1,0 +1,364 @@
+"""Python binding of the hj C ABI (include/hj.h).
+
+Argument marshalling only: every step of the solve runs in the CUDA kernels
+of libhj_gb300.so.  There is no CPU fallback.  If the library is missing or
+no CUDA device is present, the calls raise.
+
+The module-level functions carry the C names (hj_grid_create, hj_solve, ...).
+`Grid` and `solve_batch` are thin conveniences over them, and they accept
+numpy arrays and torch CUDA tensors for the value field.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhj_gb300.so")
+
+HJ_OK, HJ_ERR_ARG, HJ_ERR_OOM, HJ_ERR_CUDA = 0, 1, 2, 3
+HJ_ERR_NOT_CONVERGED, HJ_ERR_STATE, HJ_ERR_ABORTED, HJ_ERR_DIVERGED = 4, 5, 6, 7
+HJ_DRIFT, HJ_QUAD_Z, HJ_QUAD_X4 = 0, 1, 2
+HJ_FIRST, HJ_ENO2, HJ_WENO5 = 1, 2, 5
+HJ_CLAMP_VI, HJ_CLAMP_MONOTONE = 0, 1
+HJ_COLD, HJ_WARM = 0, 1
+HJ_MAX_DIM = 4
+
+STATUS_NAMES = {0: "HJ_OK", 1: "HJ_ERR_ARG", 2: "HJ_ERR_OOM", 3: "HJ_ERR_CUDA",
+                4: "HJ_ERR_NOT_CONVERGED", 5: "HJ_ERR_STATE", 6: "HJ_ERR_ABORTED",
+                7: "HJ_ERR_DIVERGED"}
+MODELS = {"drift": HJ_DRIFT, "quad_z": HJ_QUAD_Z, "quad_x4": HJ_QUAD_X4}
+
+
+class HJError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+        self.status = status
+
+
+class hj_solve_opts(ctypes.Structure):
+    _fields_ = [("scheme", ctypes.c_int), ("cfl", ctypes.c_double), ("dt", ctypes.c_double),
+                ("tol", ctypes.c_double), ("check_dt", ctypes.c_double),
+                ("max_steps", ctypes.c_longlong), ("fixed_steps", ctypes.c_longlong),
+                ("max_wall_ms", ctypes.c_double), ("clamp", ctypes.c_int),
+                ("use_graph", ctypes.c_int)]
+
+
+class hj_solve_stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_longlong), ("t", ctypes.c_double),
+                ("residual", ctypes.c_double), ("dt", ctypes.c_double),
+                ("wall_ms", ctypes.c_double), ("converged", ctypes.c_int),
+                ("windows", ctypes.c_longlong)]
+
+    def as_dict(self) -> Dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = ctypes.POINTER
+_vp, _i, _d, _ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+
+# C signatures: name -> (restype, argtypes)
+SIGNATURES = {
+    "hj_default_opts": (None, [_P(hj_solve_opts)]),
+    "hj_grid_create": (_i, [_P(_vp), _i, _P(_i), _P(_d), _P(_d), _vp]),
+    "hj_grid_destroy": (None, [_vp]),
+    "hj_set_stream": (_i, [_vp, _vp]),
+    "hj_set_dynamics": (_i, [_vp, _i, _P(_d), _i]),
+    "hj_set_constraint": (_i, [_vp, _P(_d), _P(_d)]),
+    "hj_set_constraint_ball": (_i, [_vp, _P(_d), _d]),
+    "hj_set_disturbance_bound": (_i, [_vp, _P(_d), _P(_d), _i]),
+    "hj_solve": (_i, [_vp, _i, _P(hj_solve_opts), _P(hj_solve_stats)]),
+    "hj_solve_batch": (_i, [_P(_vp), _i, _P(_i), _P(hj_solve_opts), _i, _P(hj_solve_stats),
+                            _P(_i)]),
+    "hj_prolong": (_i, [_vp, _vp]),
+    "hj_set_value": (_i, [_vp, _vp, _i]),
+    "hj_get_value": (_i, [_vp, _vp, _i]),
+    "hj_query_value": (_i, [_vp, _i, _P(_d), _P(_d)]),
+    "hj_query_gradient": (_i, [_vp, _i, _P(_d), _P(_d)]),
+    "hj_alpha": (_i, [_vp, _P(_d)]),
+    "hj_grid_points": (_ll, [_vp]),
+    "hj_last_error": (ctypes.c_char_p, []),
+    "hj_kernel_launches": (ctypes.c_ulonglong, []),
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libhj_gb300.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                "libhj_gb300.so is not built: run paper_2101_05916_gb300.build.build() "
+                "(the CUDA library is required; there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def hj_last_error() -> str:
+    m = lib().hj_last_error()
+    return m.decode() if m else ""
+
+
+def _check(status: int) -> int:
+    if status != HJ_OK:
+        raise HJError(status, hj_last_error())
+    return status
+
+
+def _darr(vals: Sequence[float]):
+    a = (ctypes.c_double * max(1, len(vals)))()
+    for i, v in enumerate(vals):
+        a[i] = float(v)
+    return a
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+# ---------------------------------------------------------------- C names
+
+def hj_default_opts() -> hj_solve_opts:
+    o = hj_solve_opts()
+    lib().hj_default_opts(ctypes.byref(o))
+    return o
+
+
+def hj_grid_create(n: Sequence[int], lo: Sequence[float], hi: Sequence[float], stream=None) -> int:
+    h = ctypes.c_void_p()
+    nd = len(n)
+    na = (ctypes.c_int * nd)(*[int(v) for v in n])
+    _check(lib().hj_grid_create(ctypes.byref(h), nd, na, _darr(lo), _darr(hi),
+                                _stream_handle(stream)))
+    return h.value
+
+
+def hj_grid_destroy(g: int) -> None:
+    lib().hj_grid_destroy(g)
+
+
+def hj_set_stream(g: int, stream) -> None:
+    _check(lib().hj_set_stream(g, _stream_handle(stream)))
+
+
+def hj_set_dynamics(g: int, model, params: Sequence[float]) -> None:
+    m = MODELS[model] if isinstance(model, str) else int(model)
+    _check(lib().hj_set_dynamics(g, m, _darr(params), len(params)))
+
+
+def hj_set_constraint(g: int, box_lo: Sequence[float], box_hi: Sequence[float]) -> None:
+    _check(lib().hj_set_constraint(g, _darr(box_lo), _darr(box_hi)))
+
+
+def hj_set_constraint_ball(g: int, centre: Sequence[float], radius: float) -> None:
+    _check(lib().hj_set_constraint_ball(g, _darr(centre), float(radius)))
+
+
+def hj_set_disturbance_bound(g: int, d_lo: Sequence[float], d_hi: Sequence[float]) -> None:
+    _check(lib().hj_set_disturbance_bound(g, _darr(d_lo), _darr(d_hi), len(d_lo)))
+
+
+def make_opts(scheme: int = HJ_WENO5, cfl: float = 0.5, dt: float = 0.0, tol: float = 1e-4,
+              check_dt: float = 0.1, max_steps: int = 1000000, fixed_steps: int = 0,
+              max_wall_ms: float = 0.0, clamp: int = HJ_CLAMP_VI,
+              use_graph: bool = True) -> hj_solve_opts:
+    return hj_solve_opts(scheme, cfl, dt, tol, check_dt, max_steps, fixed_steps, max_wall_ms,
+                         clamp, 1 if use_graph else 0)
+
+
+def hj_solve(g: int, mode: int = HJ_COLD, opts: Optional[hj_solve_opts] = None,
+             raise_on_error: bool = True):
+    """Returns (status, stats dict)."""
+    st = hj_solve_stats()
+    rc = lib().hj_solve(g, int(mode), ctypes.byref(opts) if opts is not None else None,
+                        ctypes.byref(st))
+    if raise_on_error and rc not in (HJ_OK, HJ_ERR_NOT_CONVERGED):
+        raise HJError(rc, hj_last_error())
+    return rc, st.as_dict()
+
+
+def hj_solve_batch(grids: Sequence[int], modes: Sequence[int],
+                   opts: Optional[Sequence[hj_solve_opts]] = None):
+    """Returns (first status, per-grid statuses, per-grid stats dicts)."""
+    n = len(grids)
+    ga = (ctypes.c_void_p * n)(*grids)
+    ma = (ctypes.c_int * n)(*[int(m) for m in modes])
+    if opts is None:
+        oa, oc = None, 0
+    else:
+        oa = (hj_solve_opts * len(opts))(*opts)
+        oc = len(opts)
+    sa = (hj_solve_stats * n)()
+    ra = (ctypes.c_int * n)()
+    rc = lib().hj_solve_batch(ga, n, ma, oa, oc, sa, ra)
+    if rc not in (HJ_OK, HJ_ERR_NOT_CONVERGED) and all(r == HJ_OK for r in ra):
+        raise HJError(rc, hj_last_error())
+    return rc, list(ra), [s.as_dict() for s in sa]
+
+
+def hj_prolong(coarse: int, fine: int) -> None:
+    _check(lib().hj_prolong(coarse, fine))
+
+
+def _field_ptr(buf, npts: int, writable: bool):
+    """(pointer, on_device, keepalive) for a numpy array or torch tensor of npts floats."""
+    try:
+        import torch
+        if isinstance(buf, torch.Tensor):
+            if buf.dtype != torch.float32 or not buf.is_contiguous() or buf.numel() != npts:
+                raise ValueError("need a contiguous float32 tensor of %d values" % npts)
+            return buf.data_ptr(), 1 if buf.is_cuda else 0, buf
+    except ImportError:  # pragma: no cover
+        pass
+    a = np.asarray(buf)
+    if a.dtype != np.float32 or not a.flags.c_contiguous or a.size != npts:
+        raise ValueError("need a C-contiguous float32 array of %d values" % npts)
+    if writable and not a.flags.writeable:
+        raise ValueError("array is read-only")
+    return a.ctypes.data, 0, a
+
+
+def hj_set_value(g: int, src) -> None:
+    npts = lib().hj_grid_points(g)
+    if isinstance(src, np.ndarray) and src.dtype != np.float32:
+        src = np.ascontiguousarray(src, dtype=np.float32)
+    ptr, dev, keep = _field_ptr(src, npts, False)
+    _check(lib().hj_set_value(g, ptr, dev))
+    del keep
+
+
+def hj_get_value(g: int, dst) -> None:
+    npts = lib().hj_grid_points(g)
+    ptr, dev, keep = _field_ptr(dst, npts, True)
+    _check(lib().hj_get_value(g, ptr, dev))
+    del keep
+
+
+def _points(xs, ndim):
+    a = np.ascontiguousarray(xs, dtype=np.float64).reshape(-1, ndim)
+    return a, a.ctypes.data_as(_P(_d))
+
+
+def hj_query_value(g: int, xs, ndim: int) -> np.ndarray:
+    a, p = _points(xs, ndim)
+    out = np.zeros(a.shape[0])
+    _check(lib().hj_query_value(g, a.shape[0], p, out.ctypes.data_as(_P(_d))))
+    return out
+
+
+def hj_query_gradient(g: int, xs, ndim: int) -> np.ndarray:
+    a, p = _points(xs, ndim)
+    out = np.zeros_like(a)
+    _check(lib().hj_query_gradient(g, a.shape[0], p, out.ctypes.data_as(_P(_d))))
+    return out
+
+
+def hj_alpha(g: int, ndim: int) -> np.ndarray:
+    out = (ctypes.c_double * ndim)()
+    _check(lib().hj_alpha(g, out))
+    return np.array(out[:])
+
+
+def hj_grid_points(g: int) -> int:
+    return int(lib().hj_grid_points(g))
+
+
+def hj_kernel_launches() -> int:
+    return int(lib().hj_kernel_launches())
+
+
+# ------------------------------------------------------------ conveniences
+
+class Grid:
+    """Owns one hj_grid handle."""
+
+    def __init__(self, n: Sequence[int], lo: Sequence[float], hi: Sequence[float], stream=None):
+        self.n = tuple(int(v) for v in n)
+        self.ndim = len(self.n)
+        self.handle = hj_grid_create(self.n, lo, hi, stream)
+
+    @classmethod
+    def from_spec(cls, spec, stream=None) -> "Grid":
+        """Grid, dynamics, disturbance box and constraint of a workloads.ProblemSpec."""
+        g = cls(spec.n, spec.lo, spec.hi, stream)
+        hj_set_dynamics(g.handle, spec.model, spec.params)
+        hj_set_disturbance_bound(g.handle, spec.d_lo, spec.d_hi)
+        if spec.con_kind == "box":
+            hj_set_constraint(g.handle, spec.con_a, spec.con_b)
+        else:
+            hj_set_constraint_ball(g.handle, spec.con_a, spec.con_b[0])
+        g.spec = spec
+        return g
+
+    def set_disturbance_bound(self, d_lo, d_hi) -> None:
+        hj_set_disturbance_bound(self.handle, d_lo, d_hi)
+
+    def solve(self, mode: int = HJ_COLD, **kw) -> Dict:
+        rc, st = hj_solve(self.handle, mode, make_opts(**kw))
+        st["status"] = rc
+        return st
+
+    def value(self) -> np.ndarray:
+        out = np.empty(self.n, dtype=np.float32)
+        hj_get_value(self.handle, out)
+        return out
+
+    def value_into(self, tensor) -> None:
+        hj_get_value(self.handle, tensor)
+
+    def set_value(self, src) -> None:
+        hj_set_value(self.handle, src)
+
+    def query_value(self, xs) -> np.ndarray:
+        return hj_query_value(self.handle, xs, self.ndim)
+
+    def query_gradient(self, xs) -> np.ndarray:
+        return hj_query_gradient(self.handle, xs, self.ndim)
+
+    def alpha(self) -> np.ndarray:
+        return hj_alpha(self.handle, self.ndim)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            hj_grid_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def solve_batch(grids: List[Grid], modes: Sequence[int], **kw):
+    opts = [make_opts(**kw)] if not isinstance(kw.get("per_grid"), list) else kw["per_grid"]
+    return hj_solve_batch([g.handle for g in grids], modes, opts)
+
+
+def prolong(coarse: Grid, fine: Grid) -> None:
+    hj_prolong(coarse.handle, fine.handle)
+
+
+def cfl_steps(check_dt: float, dt: float) -> int:
+    return max(1, int(math.ceil(check_dt / dt - 1e-9)))

@@ -1,0 +1,415 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerance: |W_gpu - W_oracle| <= 1e-4 * max|W_oracle|.  The sign of W must
+agree at >= 99.99 % of the nodes that lie more than one cell from the oracle's
+zero level set.  Both bounds come from the accuracy target for this solve.
+Fixed-horizon cases give both sides the same dt and the same step count.
+Converged 2-D cases run the oracle to a 1e-7 window residual and the GPU to
+1e-5, its FP32 floor; converged 4-D cases use the 1e-4 stop rule on both sides.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2101_05916_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-4
+SIGN_FRAC = 0.9999
+
+
+@pytest.fixture(scope="module")
+def hj():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2101_05916_gb300 import build, hj as hjmod
+    build.build()
+    hjmod.lib()
+    return hjmod
+
+
+def assert_parity(Wg, Wo, spec, rel=REL):
+    Wg = np.asarray(Wg, dtype=np.float64).reshape(Wo.shape)
+    scale = np.abs(Wo).max()
+    err = np.abs(Wg - Wo).max()
+    assert err <= rel * scale, "max err %.3e > %.1e * %.3e" % (err, rel, scale)
+    # sign test away from the zero level set (more than one cell in every axis)
+    near = np.zeros(Wo.shape, dtype=bool)
+    pos = Wo >= 0
+    for ax in range(Wo.ndim):
+        for sh in (1, -1):
+            rolled = np.roll(pos, sh, axis=ax)
+            edge = [slice(None)] * Wo.ndim
+            edge[ax] = slice(0, 1) if sh == 1 else slice(-1, None)
+            diff = rolled != pos
+            diff[tuple(edge)] = False
+            near |= diff
+    far = ~near & (Wo != 0)
+    if far.any():
+        agree = np.mean(np.sign(Wg[far]) == np.sign(Wo[far]))
+        assert agree >= SIGN_FRAC, "sign agreement %.6f" % agree
+
+
+def gpu_fixed(hj, spec, scheme, steps, dt=None, clamp=0, warm=None):
+    g = hj.Grid.from_spec(spec)
+    try:
+        if warm is not None:
+            g.set_value(np.ascontiguousarray(warm, dtype=np.float32))
+        if dt is None:
+            dt = oracle.cfl_dt(spec)
+        st = g.solve(hj.HJ_WARM if warm is not None else hj.HJ_COLD, scheme=scheme, dt=dt,
+                     fixed_steps=steps, clamp=clamp)
+        return g.value(), st
+    finally:
+        g.close()
+
+
+CASES_FIXED = [
+    ("z101_eno2", lambda: wl.quad_z(101, 0.5), 2, 60),
+    ("z101_weno5", lambda: wl.quad_z(101, 0.5), 5, 60),
+    ("z101_first", lambda: wl.quad_z(101, 0.5), 1, 60),
+    ("z57x83_asym", lambda: wl.dataclasses.replace(wl.quad_z(57, 0.0), n=(57, 83),
+                                                   d_lo=(-1.2,), d_hi=(0.3,)), 5, 40),
+    ("x21_weno5", lambda: wl.quad_x4(21, 0.5), 5, 12),
+    ("x21_eno2", lambda: wl.quad_x4(21, 0.5), 2, 12),
+    ("x17_axis1", lambda: wl.dataclasses.replace(
+        wl.quad_x4(17, 0.7), params=wl.X4_PARAMS[:6] + (1.0,)), 5, 10),
+    ("x13x15x9x19_ragged", lambda: wl.quad_x4(13, 0.5).with_grid((13, 15, 9, 19)), 5, 10),
+    ("drift1_ball", lambda: wl.drift((37,), 2.0, 0.5, wl.CON_BALL_OUT, r=0.3), 5, 20),
+    ("drift2_box", lambda: wl.drift((23, 29), 2.0, 0.4, wl.CON_BOX, r=1.1), 5, 20),
+    ("drift3_ball", lambda: wl.drift((11, 13, 17), 2.0, 0.4, wl.CON_BALL_OUT, r=0.5), 2, 15),
+    ("drift4_box", lambda: wl.drift((7, 9, 11, 13), 2.0, 0.3, wl.CON_BOX, r=1.0), 5, 10),
+    ("drift4_min3", lambda: wl.drift((3, 3, 3, 3), 1.0, 0.3, wl.CON_BOX, r=0.5), 5, 5),
+]
+
+
+@pytest.mark.parametrize("name,make,scheme,steps", CASES_FIXED, ids=[c[0] for c in CASES_FIXED])
+def test_fixed_horizon_parity(hj, name, make, scheme, steps):
+    spec = make()
+    dt = oracle.cfl_dt(spec)
+    Wo, _ = oracle.solve(spec, scheme=scheme, dt=dt, fixed_steps=steps)
+    Wg, st = gpu_fixed(hj, spec, scheme, steps, dt=dt)
+    assert st["steps"] == steps
+    assert_parity(Wg, Wo, spec)
+
+
+def test_monotone_clamp_parity(hj):
+    spec = wl.quad_z(61, 0.8)
+    dt = oracle.cfl_dt(spec)
+    Wo, _ = oracle.solve(spec, scheme=5, dt=dt, fixed_steps=40, clamp=1)
+    Wg, _ = gpu_fixed(hj, spec, 5, 40, dt=dt, clamp=1)
+    assert_parity(Wg, Wo, spec)
+    l = oracle.margin(spec)
+    assert np.all(Wg <= l.astype(np.float32) + 1e-6)
+
+
+def test_warm_start_from_seeded_prior_parity(hj):
+    spec = wl.quad_x4(15, 0.5)
+    prior = oracle.margin(spec) + 0.3 * wl.seeded_field(spec, 11, 0.2)
+    dt = oracle.cfl_dt(spec)
+    Wo, _ = oracle.solve(spec, scheme=5, dt=dt, fixed_steps=8, warm=prior)
+    Wg, _ = gpu_fixed(hj, spec, 5, 8, dt=dt, warm=prior)
+    assert_parity(Wg, Wo, spec)
+
+
+def test_alpha_parity(hj):
+    for spec in (wl.config0(), wl.config1(), wl.drift((5, 7), 1.0, 0.3),
+                 wl.dataclasses.replace(wl.quad_z(11, 0.0), d_lo=(-0.2,), d_hi=(1.7,))):
+        g = hj.Grid.from_spec(spec)
+        a = g.alpha()
+        g.close()
+        assert np.allclose(a, oracle.alpha(spec), rtol=2e-7, atol=1e-7)
+
+
+def test_z101_converged_parity(hj):
+    spec = wl.config0()
+    Wo, sto = oracle.solve(spec, scheme=2, tol=1e-7)
+    g = hj.Grid.from_spec(spec)
+    st = g.solve(hj.HJ_COLD, scheme=2, tol=1e-5)
+    Wg = g.value()
+    g.close()
+    assert st["converged"] and sto["converged"]
+    assert_parity(Wg, Wo, spec)
+
+
+def test_z101_converged_default_tol_matches_oracle_window_count(hj):
+    """At the configuration's own stop rule (1e-4 per 0.1 s) both sides stop
+    after the same number of windows."""
+    spec = wl.config0()
+    Wo, sto = oracle.solve(spec, scheme=2, tol=1e-4)
+    g = hj.Grid.from_spec(spec)
+    st = g.solve(hj.HJ_COLD, scheme=2, tol=1e-4)
+    Wg = g.value()
+    g.close()
+    assert st["converged"]
+    assert abs(st["windows"] - sto["windows"]) <= 1
+    assert np.abs(Wg - Wo).max() <= 1e-3 * np.abs(Wo).max()
+
+
+def test_x13_converged_parity(hj):
+    """4-D, converged at the configuration's own stop rule (1e-4 per 0.1 s) on
+    both sides: near the fixed point a window moves W by less than 1e-4, so
+    stopping a window or two apart stays inside the parity bound."""
+    spec = wl.quad_x4(13, 0.5)
+    Wo, sto = oracle.solve(spec, scheme=5, tol=1e-4, max_steps=60000)
+    g = hj.Grid.from_spec(spec)
+    st = g.solve(hj.HJ_COLD, scheme=5, tol=1e-4)
+    Wg = g.value()
+    g.close()
+    assert st["converged"] and sto["converged"]
+    assert abs(st["windows"] - sto["windows"]) <= 3, (st["windows"], sto["windows"])
+    assert_parity(Wg, Wo, spec)
+
+
+def test_warm_start_reaches_cold_fixed_point(hj):
+    """Sec. III-B on the GPU: the b = 0.5 result warm-starts the b = 1.0 solve,
+    which lands on the cold b = 1.0 fixed point in fewer steps."""
+    s05, s10 = wl.quad_z(101, 0.5), wl.quad_z(101, 1.0)
+    g = hj.Grid.from_spec(s05)
+    g.solve(hj.HJ_COLD, scheme=2, tol=1e-6)
+    g.set_disturbance_bound([-1.0], [1.0])
+    warm = g.solve(hj.HJ_WARM, scheme=2, tol=1e-6)
+    Ww = g.value()
+    cold = g.solve(hj.HJ_COLD, scheme=2, tol=1e-6)
+    Wc = g.value()
+    g.close()
+    assert warm["converged"] and cold["converged"]
+    assert warm["steps"] < cold["steps"]
+    assert np.abs(Ww - Wc).max() <= REL * np.abs(Wc).max()
+    Wo, _ = oracle.solve(s10, scheme=2, tol=1e-7)
+    assert_parity(Ww, Wo, s10)
+
+
+def test_prolongation_parity(hj):
+    c, f = wl.quad_x4(11, 1.0), wl.quad_x4(27, 1.0)
+    Wc = (oracle.margin(c) + wl.seeded_field(c, 5, 0.1)).astype(np.float32)
+    gc, gf = hj.Grid.from_spec(c), hj.Grid.from_spec(f)
+    gc.set_value(Wc)
+    hj.prolong(gc, gf)
+    Wf = gf.value()
+    gc.close()
+    gf.close()
+    Wo = oracle.prolong(c, Wc.astype(np.float64), f)
+    assert np.abs(Wf - Wo).max() <= 2e-6 * np.abs(Wo).max()
+
+
+def test_prolongation_outside_coarse_box_is_rejected(hj):
+    c = wl.quad_z(11, 0.5)
+    f = wl.dataclasses.replace(wl.quad_z(11, 0.5), hi=(3.5, 3.0))
+    gc, gf = hj.Grid.from_spec(c), hj.Grid.from_spec(f)
+    gc.solve(hj.HJ_COLD, scheme=2, fixed_steps=1)
+    with pytest.raises(hj.HJError) as e:
+        hj.prolong(gc, gf)
+    assert e.value.status == hj.HJ_ERR_ARG
+    gc.close()
+    gf.close()
+
+
+def test_query_parity(hj):
+    spec = wl.quad_x4(13, 0.5)
+    W = (oracle.margin(spec) + wl.seeded_field(spec, 9, 0.05)).astype(np.float32)
+    g = hj.Grid.from_spec(spec)
+    g.set_value(W)
+    rng = np.random.default_rng(4)
+    xs = rng.uniform(spec.lo, spec.hi, size=(257, 4))
+    v = g.query_value(xs)
+    gr = g.query_gradient(xs)
+    with pytest.raises(hj.HJError):
+        g.query_value(np.array([[6.0, 0, 0, 0]]))
+    assert g.query_value(np.zeros((0, 4))).shape == (0,)
+    g.close()
+    W64 = W.astype(np.float64)
+    assert np.allclose(v, oracle.query_value(spec, W64, xs), rtol=1e-12, atol=1e-12)
+    assert np.allclose(gr, oracle.query_gradient(spec, W64, xs), rtol=1e-10, atol=1e-10)
+
+
+def test_batch_equals_single_grid_bitwise(hj):
+    """The fused multi-grid launch runs the same per-node code, so every grid
+    of a batch ends bit-identical to its own single-grid solve."""
+    specs = [wl.quad_x4(17, 0.5, 4.0, "x"), wl.quad_x4(17, 0.5, 3.5, "y"), wl.quad_z(61, 0.5)]
+    schemes = [5, 5, 2]
+    singles = []
+    for s, sc in zip(specs, schemes):
+        g = hj.Grid.from_spec(s)
+        st = g.solve(hj.HJ_COLD, scheme=sc, tol=1e-4, max_steps=3000)
+        singles.append((g.value(), st))
+        g.close()
+    grids = [hj.Grid.from_spec(s) for s in specs]
+    opts = [hj.make_opts(scheme=sc, tol=1e-4, max_steps=3000) for sc in schemes]
+    rc, statuses, stats = hj.hj_solve_batch([g.handle for g in grids], [0, 0, 0], opts)
+    for g, (Ws, sts), stb in zip(grids, singles, stats):
+        Wb = g.value()
+        assert stb["steps"] == sts["steps"]
+        assert np.array_equal(Wb, Ws)
+        g.close()
+
+
+def test_x_and_y_identical_inputs_identical_results(hj):
+    s = wl.quad_x4(15, 0.5, 3.5)
+    a, b = hj.Grid.from_spec(s), hj.Grid.from_spec(s)
+    rc, _, st = hj.hj_solve_batch([a.handle, b.handle], [0, 0], [hj.make_opts(fixed_steps=30)])
+    assert np.array_equal(a.value(), b.value())
+    a.close()
+    b.close()
+
+
+# ------------------------------------------------------------ full sizes
+
+def test_config1_full_size_fixed_horizon(hj):
+    """41^4, WENO5, five steps from the cold start, in the bench's launch shape."""
+    spec = wl.config1()
+    dt = oracle.cfl_dt(spec)
+    Wo, _ = oracle.solve(spec, scheme=5, dt=dt, fixed_steps=5)
+    Wg, _ = gpu_fixed(hj, spec, 5, 5, dt=dt)
+    assert_parity(Wg, Wo, spec)
+
+
+def test_config2_batch_full_size_fixed_horizon(hj):
+    """x, y at 61^4 and z at 201^2 as one fused batch, two steps each, sampled
+    against the oracle on every node of each grid."""
+    specs = [s.with_bound(0.5) for s in wl.config2()]
+    schemes = [5, 5, 2]
+    grids = [hj.Grid.from_spec(s) for s in specs]
+    dts = [oracle.cfl_dt(s) for s in specs]
+    opts = [hj.make_opts(scheme=sc, dt=dt, fixed_steps=2) for sc, dt in zip(schemes, dts)]
+    rc, statuses, stats = hj.hj_solve_batch([g.handle for g in grids], [0, 0, 0], opts)
+    assert all(s == 0 for s in statuses)
+    for g, s, sc, dt in zip(grids, specs, schemes, dts):
+        Wo, _ = oracle.solve(s, scheme=sc, dt=dt, fixed_steps=2)
+        assert_parity(g.value(), Wo, s)
+        g.close()
+
+
+def test_config3_prolong_full_size_sampled(hj):
+    """31^4 -> 81^4 prolongation of a seeded coarse field, checked against the
+    oracle's interpolation at 4096 sampled fine nodes."""
+    c, f, _ = wl.config3()
+    Wc = (oracle.margin(c) + wl.seeded_field(c, 21, 0.05)).astype(np.float32)
+    gc, gf = hj.Grid.from_spec(c), hj.Grid.from_spec(f)
+    gc.set_value(Wc)
+    hj.prolong(gc, gf)
+    Wf = gf.value()
+    gc.close()
+    gf.close()
+    rng = np.random.default_rng(8)
+    idx = rng.integers(0, 81, size=(4096, 4))
+    X = [np.linspace(a, b, m) for a, b, m in zip(f.lo, f.hi, f.n)]
+    pts = np.stack([X[d][idx[:, d]] for d in range(4)], axis=1)
+    vo = oracle.query_value(c, Wc.astype(np.float64), pts)
+    lo = np.array([oracle.margin_at(f, p) for p in pts])
+    expect = np.minimum(vo, lo)
+    got = Wf[idx[:, 0], idx[:, 1], idx[:, 2], idx[:, 3]]
+    assert np.abs(got - expect).max() <= 2e-6 * np.abs(expect).max()
+
+
+def test_converged_full_size_properties(hj):
+    """41^4 converged cold solve: W <= l everywhere, W even under the point
+    reflection of the symmetric x-subsystem, and the warm solve from the b = 0
+    fixed point lands on the cold b = 0.5 fixed point."""
+    s0, s5 = wl.config1(b=0.0), wl.config1(b=0.5)
+    g = hj.Grid.from_spec(s0)
+    cap = dict(scheme=5, max_steps=100000, max_wall_ms=120000.0)
+    st0 = g.solve(hj.HJ_COLD, **cap)
+    assert st0["converged"]
+    g.set_disturbance_bound([-0.5], [0.5])
+    stw = g.solve(hj.HJ_WARM, **cap)
+    Ww = g.value()
+    stc = g.solve(hj.HJ_COLD, **cap)
+    Wc = g.value()
+    g.close()
+    assert stw["converged"] and stc["converged"]
+    assert stw["steps"] < stc["steps"]
+    l = oracle.margin(s5).astype(np.float32)
+    assert np.all(Wc <= l)
+    assert np.abs(Wc - Wc[::-1, ::-1, ::-1, ::-1]).max() <= 1e-4 * np.abs(Wc).max()
+    assert np.abs(Ww - Wc).max() <= 2e-3 * np.abs(Wc).max()
+
+
+# ------------------------------------------------------------ edges
+
+def test_argument_errors(hj):
+    with pytest.raises(hj.HJError) as e:
+        hj.hj_grid_create([2, 5], [0, 0], [1, 1])
+    assert e.value.status == hj.HJ_ERR_ARG
+    with pytest.raises(hj.HJError):
+        hj.hj_grid_create([5], [1.0], [0.0])
+    with pytest.raises(hj.HJError):
+        hj.hj_grid_create([2000, 2000, 1000], [0, 0, 0], [1, 1, 1])  # >= 2^31 nodes
+    g = hj.Grid([5, 5], [0, 0], [1, 1])
+    rc, _ = hj.hj_solve(g.handle, 0, hj.make_opts(), raise_on_error=False)
+    assert rc == hj.HJ_ERR_STATE
+    hj.hj_set_dynamics(g.handle, "drift", [])
+    hj.hj_set_constraint(g.handle, [0.2, -np.inf], [0.8, np.inf])
+    rc, _ = hj.hj_solve(g.handle, 0, hj.make_opts(), raise_on_error=False)
+    assert rc == hj.HJ_ERR_STATE  # disturbance not set
+    hj.hj_set_disturbance_bound(g.handle, [-0.1, -0.1], [0.1, 0.1])
+    rc, _ = hj.hj_solve(g.handle, 1, hj.make_opts(), raise_on_error=False)
+    assert rc == hj.HJ_ERR_STATE  # warm without a prior
+    with pytest.raises(hj.HJError):
+        hj.hj_set_dynamics(g.handle, "quad_x4", list(wl.X4_PARAMS))  # wrong ndim
+    g.close()
+
+
+def test_step_cap_returns_not_converged_with_valid_tube(hj):
+    spec = wl.quad_z(61, 0.5)
+    g = hj.Grid.from_spec(spec)
+    st = g.solve(hj.HJ_COLD, scheme=2, tol=1e-9, max_steps=17)
+    assert st["status"] == hj.HJ_ERR_NOT_CONVERGED and st["steps"] == 17
+    Wg = g.value()
+    g.close()
+    Wo, _ = oracle.solve(spec, scheme=2, dt=st["dt"], fixed_steps=17)
+    assert_parity(Wg, Wo, spec)
+
+
+def test_no_motion_converges_immediately(hj):
+    spec = wl.drift((9, 9), 1.0, 0.0, wl.CON_BOX, r=0.5)
+    g = hj.Grid.from_spec(spec)
+    st = g.solve(hj.HJ_COLD, scheme=5)
+    W = g.value()
+    g.close()
+    assert st["converged"] and st["steps"] == 0
+    assert np.allclose(W, oracle.margin(spec), atol=1e-6)
+
+
+def test_graph_and_direct_launch_agree(hj):
+    spec = wl.quad_z(81, 0.5)
+    out = []
+    for graph in (True, False):
+        g = hj.Grid.from_spec(spec)
+        st = g.solve(hj.HJ_COLD, scheme=5, tol=1e-4, use_graph=graph)
+        out.append((g.value(), st["steps"]))
+        g.close()
+    assert out[0][1] == out[1][1]
+    assert np.array_equal(out[0][0], out[1][0])
+
+
+def test_device_pointer_io_and_stream(hj):
+    import torch
+    spec = wl.quad_z(41, 0.5)
+    s = torch.cuda.Stream()
+    g = hj.Grid.from_spec(spec, stream=s)
+    t = torch.full((41 * 41,), 0.25, device="cuda", dtype=torch.float32)
+    g.set_value(t)
+    out = torch.empty_like(t)
+    g.value_into(out)
+    assert torch.equal(out, t)
+    st = g.solve(hj.HJ_WARM, scheme=2, fixed_steps=3)
+    g.value_into(out)
+    torch.cuda.synchronize()
+    W = out.cpu().numpy().reshape(41, 41)
+    g.close()
+    prior = np.full((41, 41), 0.25)
+    Wo, _ = oracle.solve(spec, scheme=2, dt=st["dt"], fixed_steps=3, warm=prior)
+    assert_parity(W, Wo, spec)
+
+
+def test_kernel_launch_counter_moves(hj):
+    before = hj.hj_kernel_launches()
+    spec = wl.quad_z(21, 0.5)
+    g = hj.Grid.from_spec(spec)
+    g.solve(hj.HJ_COLD, scheme=2, fixed_steps=4)
+    g.close()
+    assert hj.hj_kernel_launches() - before >= 12
