@@ -29,7 +29,8 @@
  *   - Time step: dt = cfl / sum_i(a_i / h_i), where a_i is the largest |f_i|
  *     over the grid and the input boxes.
  *   - Integration: TVD-RK3, then the clamp after each full step.
- *   - Stop: when max|W(t + check_dt) - W(t)| < tol.
+ *   - Stop: when max|W(t + check_dt) - W(t)| < tol, over every node or over
+ *     the band |W| <= opts.band around the zero level set.
  *
  * Threading and memory:
  *   - Handles are not thread-safe.  Use one handle per thread, or serialise
@@ -96,6 +97,10 @@ typedef struct {
   double max_wall_ms;    /* wall-time cap checked between windows, 0 = none               */
   int clamp;             /* HJ_CLAMP_VI (default) or HJ_CLAMP_MONOTONE                    */
   int use_graph;         /* 1: replay each window as a captured CUDA graph (default 1)    */
+  double band;           /* > 0: the stop test watches only nodes with                    */
+                         /* min(|W|, |W_window_start|) <= band, i.e. the band around the  */
+                         /* zero level set that bounds the safe set (Sec. II-A).          */
+                         /* 0 (default): every node.                                      */
 } hj_solve_opts;
 
 typedef struct {

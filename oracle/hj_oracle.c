@@ -20,7 +20,10 @@
  *
  * integrated in backward time s until the change over a check window falls
  * below a tolerance (Sec. II-A: iterate "until convergence"; the converged
- * value is the infinite-horizon fixed point).
+ * value is the infinite-horizon fixed point).  Optionally the stop test only
+ * watches a band |W| <= band around the zero level set that bounds the safe
+ * set S (Sec. II-A); far inside S, high-order schemes on a truncated grid can
+ * keep cycling without moving S.
  *
  * The paper names no numerical scheme.  The discrete operator below is the
  * textbook one (Osher & Fedkiw 2003, Sec. 3.3-3.4 and 5.3; Jiang & Peng 2000;
@@ -90,6 +93,8 @@ typedef struct {
   long fixed_steps;  /* > 0: run exactly this many steps, no stop test    */
   int clamp;
   int warm;          /* 0 = start from l, 1 = start from min(W_in, l)     */
+  double band;       /* > 0: the stop test only watches nodes with
+                        min(|W|, |W_window_start|) <= band                 */
 } or_opts;
 
 typedef struct {
@@ -439,6 +444,7 @@ int or_solve(const or_problem* P, const or_opts* o, double* W, or_stats* st) {
       st->windows += 1;
       double r = 0.0;
       for (long i = 0; i < npts; ++i) {
+        if (o->band > 0.0 && fmin(fabs(W[i]), fabs(snap[i])) > o->band) continue;
         double e = fabs(W[i] - snap[i]);
         if (e > r) r = e;
       }

@@ -122,10 +122,11 @@ static void invalidate(hj_grid g) {
 
 // k TVD-RK3 steps; the last one folds the window residual when check_last.
 static cudaError_t enqueue_steps(hj_grid g, const hjd::DevGrid& d, int scheme, int clamp,
-                                 float dt, long long k, bool check_last, cudaStream_t s) {
-  hjd::StageArgs a1{g->W, g->W, g->A, nullptr, nullptr, dt, 0, clamp};
-  hjd::StageArgs a2{g->A, g->W, g->B, nullptr, nullptr, dt, 0, clamp};
-  hjd::StageArgs a3{g->B, g->W, g->W, g->snap, g->dscal + 4, dt, 0, clamp};
+                                 float band, float dt, long long k, bool check_last,
+                                 cudaStream_t s) {
+  hjd::StageArgs a1{g->W, g->W, g->A, nullptr, nullptr, dt, 0, clamp, band};
+  hjd::StageArgs a2{g->A, g->W, g->B, nullptr, nullptr, dt, 0, clamp, band};
+  hjd::StageArgs a3{g->B, g->W, g->W, g->snap, g->dscal + 4, dt, 0, clamp, band};
   for (long long i = 0; i < k; ++i) {
     cudaError_t e;
     if ((e = hjk::launch_stage(d, scheme, 1, a1, s)) != cudaSuccess) return e;
@@ -137,24 +138,24 @@ static cudaError_t enqueue_steps(hj_grid g, const hjd::DevGrid& d, int scheme, i
 }
 
 // One check window: reset the residual, k steps, copy the residual to pinned host memory.
-static cudaError_t enqueue_window(hj_grid g, const hjd::DevGrid& d, int scheme, int clamp, float dt,
-                                  long long k, cudaStream_t s) {
+static cudaError_t enqueue_window(hj_grid g, const hjd::DevGrid& d, int scheme, int clamp,
+                                  float band, float dt, long long k, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(g->dscal + 4, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
-  if ((e = enqueue_steps(g, d, scheme, clamp, dt, k, true, s)) != cudaSuccess) return e;
+  if ((e = enqueue_steps(g, d, scheme, clamp, band, dt, k, true, s)) != cudaSuccess) return e;
   return cudaMemcpyAsync(g->hscal + 4, g->dscal + 4, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
 }
 
-static hj_status run_window(hj_grid g, const hjd::DevGrid& d, int scheme, int clamp, float dt,
-                            long long k, bool use_graph) {
+static hj_status run_window(hj_grid g, const hjd::DevGrid& d, int scheme, int clamp, float band,
+                            float dt, long long k, bool use_graph) {
   if (use_graph && k <= 4096) {
     if (!(g->gexec && g->g_per == k && g->g_dt == dt && g->g_scheme == scheme &&
-          g->g_clamp == clamp)) {
+          g->g_clamp == clamp && g->g_band == band)) {
       drop_graph(g);
       cudaGraph_t graph = nullptr;
       HJ_CU(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
       unsigned long long before = hjk::g_launches.load();
-      cudaError_t e = enqueue_window(g, d, scheme, clamp, dt, k, g->cap_stream);
+      cudaError_t e = enqueue_window(g, d, scheme, clamp, band, dt, k, g->cap_stream);
       cudaError_t e2 = cudaStreamEndCapture(g->cap_stream, &graph);
       // launches recorded during capture run later, on replay
       hjk::g_launches.store(before);
@@ -173,11 +174,12 @@ static hj_status run_window(hj_grid g, const hjd::DevGrid& d, int scheme, int cl
       g->g_dt = dt;
       g->g_scheme = scheme;
       g->g_clamp = clamp;
+      g->g_band = band;
     }
     HJ_CU(cudaGraphLaunch(g->gexec, g->stream));
     hjk::g_launches.fetch_add(3ull * (unsigned long long)k);
   } else {
-    HJ_CU(enqueue_window(g, d, scheme, clamp, dt, k, g->stream));
+    HJ_CU(enqueue_window(g, d, scheme, clamp, band, dt, k, g->stream));
   }
   HJ_CU(cudaStreamSynchronize(g->stream));
   return HJ_OK;
@@ -213,6 +215,7 @@ void hj_default_opts(hj_solve_opts* o) {
   o->max_wall_ms = 0.0;
   o->clamp = HJ_CLAMP_VI;
   o->use_graph = 1;
+  o->band = 0.0;
 }
 
 void hj_grid_destroy(hj_grid g) {
@@ -400,7 +403,7 @@ hj_status hj_solve(hj_grid g, int mode, const hj_solve_opts* o_in, hj_solve_stat
   hj_default_opts(&o);
   if (o_in) o = *o_in;
   if (mode != HJ_COLD && mode != HJ_WARM) return fail(HJ_ERR_ARG, "mode must be HJ_COLD or HJ_WARM");
-  if (!(o.cfl > 0.0) || !(o.tol >= 0.0) || !(o.check_dt > 0.0) || o.dt < 0.0)
+  if (!(o.cfl > 0.0) || !(o.tol >= 0.0) || !(o.check_dt > 0.0) || o.dt < 0.0 || !(o.band >= 0.0))
     return fail(HJ_ERR_ARG, "bad solve options");
   if (o.clamp != HJ_CLAMP_VI && o.clamp != HJ_CLAMP_MONOTONE) return fail(HJ_ERR_ARG, "bad clamp");
   hj_status st = validate_ready(g, o.scheme);
@@ -424,7 +427,8 @@ hj_status hj_solve(hj_grid g, int mode, const hj_solve_opts* o_in, hj_solve_stat
     HJ_CU(cudaStreamSynchronize(g->stream));
     stats.converged = 1;
   } else if (o.fixed_steps > 0) {
-    HJ_CU(enqueue_steps(g, d, o.scheme, o.clamp, fdt, o.fixed_steps, false, g->stream));
+    HJ_CU(enqueue_steps(g, d, o.scheme, o.clamp, (float)o.band, fdt, o.fixed_steps, false,
+                        g->stream));
     HJ_CU(cudaStreamSynchronize(g->stream));
     stats.steps = o.fixed_steps;
   } else {
@@ -433,7 +437,8 @@ hj_status hj_solve(hj_grid g, int mode, const hj_solve_opts* o_in, hj_solve_stat
     for (;;) {
       long long todo = per;
       if (o.max_steps > 0 && stats.steps + todo > o.max_steps) todo = o.max_steps - stats.steps;
-      st = run_window(g, d, o.scheme, o.clamp, fdt, todo, o.use_graph != 0 && todo == per);
+      st = run_window(g, d, o.scheme, o.clamp, (float)o.band, fdt, todo,
+                      o.use_graph != 0 && todo == per);
       if (st != HJ_OK) return st;
       stats.steps += todo;
       stats.windows += 1;

@@ -156,7 +156,7 @@ hj_status Runner::add(hj_grid g, int mode, const hj_solve_opts& o, int* slot_out
   if (!g) return hja::fail(HJ_ERR_ARG, "grid is NULL");
   if (g->device != device_) return hja::fail(HJ_ERR_ARG, "batch grids must share one device");
   if (mode != HJ_COLD && mode != HJ_WARM) return hja::fail(HJ_ERR_ARG, "bad mode");
-  if (!(o.cfl > 0.0) || !(o.tol >= 0.0) || !(o.check_dt > 0.0) || o.dt < 0.0)
+  if (!(o.cfl > 0.0) || !(o.tol >= 0.0) || !(o.check_dt > 0.0) || o.dt < 0.0 || !(o.band >= 0.0))
     return hja::fail(HJ_ERR_ARG, "bad solve options");
   hj_status st = hja::validate_ready(g, o.scheme);
   if (st != HJ_OK) return st;
@@ -188,6 +188,7 @@ hj_status Runner::add(hj_grid g, int mode, const hj_solve_opts& o, int* slot_out
   s.used = true;
   s.scheme = o.scheme;
   s.clamp = o.clamp;
+  s.band = (float)o.band;
   s.dt = dt;
   s.max_wall_ms = o.max_wall_ms;
   s.t0 = std::chrono::steady_clock::now();
@@ -246,9 +247,9 @@ hj_status Runner::rebuild() {
     std::memset(&it, 0, sizeof(it));
     it.g = hja::devgrid(g);
     float dt = (float)s.dt;
-    it.a[0] = hjd::StageArgs{g->W, g->W, g->A, nullptr, nullptr, dt, 0, s.clamp};
-    it.a[1] = hjd::StageArgs{g->A, g->W, g->B, nullptr, nullptr, dt, 0, s.clamp};
-    it.a[2] = hjd::StageArgs{g->B, g->W, g->W, g->snap, nullptr, dt, 1, s.clamp};
+    it.a[0] = hjd::StageArgs{g->W, g->W, g->A, nullptr, nullptr, dt, 0, s.clamp, s.band};
+    it.a[1] = hjd::StageArgs{g->A, g->W, g->B, nullptr, nullptr, dt, 0, s.clamp, s.band};
+    it.a[2] = hjd::StageArgs{g->B, g->W, g->W, g->snap, nullptr, dt, 1, s.clamp, s.band};
     it.kind = kind_code(g->model, g->ndim, s.scheme);
     it.slot = k;
     it.bx = (it.g.plane + kThreads - 1) / kThreads;

@@ -57,6 +57,7 @@ struct StageArgs {
   float dt;
   int check;
   int clamp;           // 0: min(W3, l); 1: min(W3, l, W)
+  float band;          // > 0: residual only where min(|W|, |snap|) <= band
 };
 
 __device__ __forceinline__ float rcp_approx(float x) {

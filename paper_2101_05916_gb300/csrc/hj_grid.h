@@ -43,6 +43,7 @@ struct hj_grid_s {
   long long g_per = 0;
   float g_dt = 0.f;
   int g_scheme = 0, g_clamp = 0;
+  float g_band = 0.f;
 };
 
 namespace hja {

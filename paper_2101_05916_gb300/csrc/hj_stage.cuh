@@ -72,8 +72,11 @@ __device__ __forceinline__ unsigned stage_point(const DevGrid& g, const StageArg
     if (w3 != w3) wn = w3;  // keep a NaN visible to the stop test
     a.dst[p] = wn;
     if (!check) return 0u;
-    float r = fabsf(wn - a.snap[p]);
+    float sv = a.snap[p];
+    float r = fabsf(wn - sv);
     a.snap[p] = wn;
+    if (a.band > 0.f && fminf(fabsf(wn), fabsf(sv)) > a.band) r = 0.f;
+    if (wn != wn) r = wn;  // NaN always reaches the stop test
     return __float_as_uint(r);
   }
 }

@@ -45,7 +45,7 @@ class hj_solve_opts(ctypes.Structure):
                 ("tol", ctypes.c_double), ("check_dt", ctypes.c_double),
                 ("max_steps", ctypes.c_longlong), ("fixed_steps", ctypes.c_longlong),
                 ("max_wall_ms", ctypes.c_double), ("clamp", ctypes.c_int),
-                ("use_graph", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("band", ctypes.c_double)]
 
 
 class hj_solve_stats(ctypes.Structure):
@@ -176,9 +176,9 @@ def hj_set_disturbance_bound(g: int, d_lo: Sequence[float], d_hi: Sequence[float
 def make_opts(scheme: int = HJ_WENO5, cfl: float = 0.5, dt: float = 0.0, tol: float = 1e-4,
               check_dt: float = 0.1, max_steps: int = 1000000, fixed_steps: int = 0,
               max_wall_ms: float = 0.0, clamp: int = HJ_CLAMP_VI,
-              use_graph: bool = True) -> hj_solve_opts:
+              use_graph: bool = True, band: float = 0.0) -> hj_solve_opts:
     return hj_solve_opts(scheme, cfl, dt, tol, check_dt, max_steps, fixed_steps, max_wall_ms,
-                         clamp, 1 if use_graph else 0)
+                         clamp, 1 if use_graph else 0, band)
 
 
 def hj_solve(g: int, mode: int = HJ_COLD, opts: Optional[hj_solve_opts] = None,

@@ -306,12 +306,13 @@ def test_config3_prolong_full_size_sampled(hj):
 
 
 def test_converged_full_size_properties(hj):
-    """41^4 converged cold solve: W <= l everywhere, W even under the point
-    reflection of the symmetric x-subsystem, and the warm solve from the b = 0
-    fixed point lands on the cold b = 0.5 fixed point."""
+    """41^4 cold solve converged on the band |W| <= 0.5 around the safe-set
+    boundary: W <= l everywhere, W even under the point reflection of the
+    symmetric x-subsystem, and the warm solve from the b = 0 fixed point
+    lands on the cold b = 0.5 one inside the band."""
     s0, s5 = wl.config1(b=0.0), wl.config1(b=0.5)
     g = hj.Grid.from_spec(s0)
-    cap = dict(scheme=5, max_steps=100000, max_wall_ms=120000.0)
+    cap = dict(scheme=5, max_steps=100000, max_wall_ms=120000.0, band=0.5)
     st0 = g.solve(hj.HJ_COLD, **cap)
     assert st0["converged"]
     g.set_disturbance_bound([-0.5], [0.5])
@@ -324,8 +325,10 @@ def test_converged_full_size_properties(hj):
     assert stw["steps"] < stc["steps"]
     l = oracle.margin(s5).astype(np.float32)
     assert np.all(Wc <= l)
-    assert np.abs(Wc - Wc[::-1, ::-1, ::-1, ::-1]).max() <= 1e-4 * np.abs(Wc).max()
-    assert np.abs(Ww - Wc).max() <= 2e-3 * np.abs(Wc).max()
+    band = np.abs(Wc) <= 0.5
+    assert np.abs(Wc - Wc[::-1, ::-1, ::-1, ::-1])[band].max() <= 1e-4 * np.abs(Wc).max()
+    assert np.abs(Ww - Wc)[band].max() <= 1e-3 * np.abs(Wc).max()
+    assert np.mean((Ww >= 0) == (Wc >= 0)) >= 0.9999
 
 
 # ------------------------------------------------------------ edges

@@ -302,6 +302,20 @@ def test_x_and_y_same_model_same_result():
     assert np.array_equal(Wx, Wy)
 
 
+def test_band_stop_test_reduces_to_full_test_and_never_stops_later():
+    """A band wider than max|W| is the full-grid test; a narrow band stops at
+    the same window or earlier, with the zero level set already in place."""
+    s = wl.quad_z(61, 0.5)
+    Wf, stf = oracle.solve(s, scheme=2, tol=1e-4)
+    Wb, stb = oracle.solve(s, scheme=2, tol=1e-4, band=100.0)
+    assert stb["steps"] == stf["steps"] and np.array_equal(Wf, Wb)
+    Wn, stn = oracle.solve(s, scheme=2, tol=1e-4, band=0.25)
+    assert stn["converged"] and stn["steps"] <= stf["steps"]
+    Wc, _ = oracle.solve(s, scheme=2, tol=1e-8)
+    near = np.abs(Wc) < 0.25
+    assert np.abs(Wn - Wc)[near].max() < 5e-3
+
+
 def test_no_motion_is_already_converged():
     s = wl.drift((11,), 1.0, 0.0, wl.CON_BOX, r=0.5)
     W, st = oracle.solve(s, scheme=2)
