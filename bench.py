@@ -53,6 +53,10 @@ FLOPS_PER_UPDATE = {("quad_x4", 5): 1624.0}
 # Compulsory DRAM bytes per update: stage 1 reads W, writes W1 (8 B); stage 2
 # reads W1, W, writes W2 (12 B); stage 3 reads W2, W, writes W (12 B).
 BYTES_PER_UPDATE = 32.0
+# DRAM bytes per stage launch (read + write, average of stages 1-3) from the
+# ncu capture summarised in profiles/stage_kernel_x41_weno5.md; set to None
+# whenever the stage kernel changes until it is captured again.
+STAGE_TRAFFIC_BYTES = (11.323904e6 + 22.627328e6 + 22.630656e6) / 3.0
 # FP32 non-tensor peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
@@ -335,7 +339,8 @@ def main():
         "peak_source": "FP32 lanes x max SM clock (152 x 128 x 2 x 2.07 GHz)",
         "per_launch_us": per_launch_s * 1e6,
         "flops_per_update": FLOPS_PER_UPDATE[("quad_x4", 5)],
-        "traffic": None,
+        "traffic": STAGE_TRAFFIC_BYTES,
+        "algorithmic_bytes_per_launch": BYTES_PER_UPDATE / 3.0 * npts,
         "hbm_view": {"achieved_gbs": hbm_gbs, "bytes_per_update": BYTES_PER_UPDATE,
                      "peak_gbs": peaks["hbm_gbs"] if peaks else 6800.0,
                      "frac": hbm_gbs / (peaks["hbm_gbs"] if peaks else 6800.0),
