@@ -207,6 +207,53 @@ hj_status hj_query_gradient(hj_grid g, int npts, const double* x, double* grad_o
  * the device by a max-reduction.  alpha_out has ndim entries. */
 hj_status hj_alpha(hj_grid g, double* alpha_out);
 
+/* Allocation-free fixed-horizon solve.  The paper has no counterpart: this
+ * entry point exists for callers that must not allocate device memory after
+ * start-up.  One example is a real-time safety filter running beside a
+ * controller, as in the paper's ROS set-up: cudaMalloc and cudaFree can
+ * synchronise the whole device and take unbounded time.  Another example is
+ * a process whose device memory is owned entirely by another framework's
+ * pool.
+ *
+ * What it does: the same computation as hj_grid_create + hj_set_dynamics +
+ * hj_set_disturbance_bound + hj_set_constraint (box) + hj_solve with
+ * opts.fixed_steps = steps, but with no handle:
+ *   - W is caller-owned device memory with npts = n[0]*..*n[ndim-1] floats.
+ *     With HJ_WARM it holds the prior on entry (HJ_COLD ignores it).  On
+ *     return it holds the value after `steps` TVD-RK3 steps.
+ *   - dt <= 0 selects the CFL step with cfl = 0.5.
+ *   - clamp is HJ_CLAMP_VI or HJ_CLAMP_MONOTONE.
+ *   - The call returns after the work on cuda_stream has finished.
+ *
+ * Where the scratch lives: the working memory is one file-scope device
+ * array, shared by every call in the process.  It holds the Lax-Friedrichs
+ * coefficient accumulator, the g tan(th) table and the two Runge-Kutta stage
+ * fields.  Every GPU that loads the library holds the array (about 32 MiB)
+ * until the process exits.
+ *
+ * Limits: at most HJ_STATIC_MAX_POINTS nodes and at most HJ_STATIC_MAX_AXIS
+ * nodes on the theta axis of HJ_QUAD_X4.  Larger problems fail with
+ * HJ_ERR_ARG before any device work.
+ *
+ * The call never calls cudaMalloc, cudaFree or any allocating library
+ * routine.
+ *
+ * First call on a device: it looks up the array's device address with that
+ * device current.  Make that first call before any stream capture.
+ *
+ * Concurrency: the array keeps the contents of the last call.  The call
+ * clears what must start at zero itself.  Calls whose GPU work overlaps
+ * (other streams, other host threads) race on the shared array and corrupt
+ * each other's results; serialise them. */
+#define HJ_STATIC_MAX_POINTS 4194304
+#define HJ_STATIC_MAX_AXIS 4096
+hj_status hj_solve_fixed_static(int ndim, const int* n, const double* lo, const double* hi,
+                                int model, const double* params, int nparams,
+                                const double* d_lo, const double* d_hi, int nd,
+                                const double* box_lo, const double* box_hi, int mode,
+                                int scheme, double dt, long long steps, int clamp, float* W,
+                                void* cuda_stream);
+
 /* Number of nodes of the grid. */
 long long hj_grid_points(hj_grid g);
 

@@ -83,6 +83,8 @@ SIGNATURES = {
     "hj_grid_points": (_ll, [_vp]),
     "hj_last_error": (ctypes.c_char_p, []),
     "hj_kernel_launches": (ctypes.c_ulonglong, []),
+    "hj_solve_fixed_static": (_i, [_i, _P(_i), _P(_d), _P(_d), _i, _P(_d), _i, _P(_d), _P(_d),
+                                   _i, _P(_d), _P(_d), _i, _i, _d, _ll, _i, _vp, _vp]),
 }
 
 _lib = None
@@ -272,6 +274,27 @@ def hj_alpha(g: int, ndim: int) -> np.ndarray:
     out = (ctypes.c_double * ndim)()
     _check(lib().hj_alpha(g, out))
     return np.array(out[:])
+
+
+def hj_solve_fixed_static(spec, W, mode: int = HJ_COLD, scheme: int = HJ_WENO5,
+                          dt: float = 0.0, steps: int = 1, clamp: int = HJ_CLAMP_VI,
+                          stream=None) -> None:
+    """Allocation-free fixed-horizon solve of a box-constrained problem into the
+    caller's device tensor W (float32, spec.npts values)."""
+    if spec.con_kind != "box":
+        raise ValueError("the allocation-free entry point takes box constraints")
+    nd = len(spec.n)
+    na = (ctypes.c_int * nd)(*[int(v) for v in spec.n])
+    m = MODELS[spec.model]
+    ptr, dev, keep = _field_ptr(W, int(np.prod(spec.n)), True)
+    if not dev:
+        raise ValueError("W must be device memory")
+    _check(lib().hj_solve_fixed_static(nd, na, _darr(spec.lo), _darr(spec.hi), m,
+                                       _darr(spec.params), len(spec.params), _darr(spec.d_lo),
+                                       _darr(spec.d_hi), len(spec.d_lo), _darr(spec.con_a),
+                                       _darr(spec.con_b), int(mode), int(scheme), float(dt),
+                                       int(steps), int(clamp), ptr, _stream_handle(stream)))
+    del keep
 
 
 def hj_grid_points(g: int) -> int:
