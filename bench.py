@@ -1,9 +1,9 @@
 """Benchmark: HJ grid-point updates/s of the safe-set solve on GB300.
 
 Workload (default): the 4-D x-subsystem of the decomposed near-hover
-quadcopter on a 41^4 grid, WENO5 + TVD-RK3, CFL 0.5, stop at an L-inf change
-below 1e-4 per 0.1 s window on the band |W| <= 0.5 around the safe-set
-boundary, wind bound |d| <= 0.5.  One bench step is one
+quadcopter on a 41^4 grid, WENO5 + TVD-RK3, CFL 0.5, clamp min(W3, l, W_prev)
+(the monotone tube), stop at an L-inf change below 1e-4 per 0.1 s window on
+the band |W| <= 0.5 around the safe-set boundary, wind bound |d| <= 0.5.  One bench step is one
 safe-set update pair:
     (1) a cold solve from the constraint margin, to convergence;
     (2) a warm-started update (Sec. III-B) from the device-resident fixed
@@ -42,6 +42,7 @@ UNIT = "grid-point updates/s"
 N_AXIS = 41
 BOUND_PRIOR, BOUND = 0.0, 0.5
 BAND = 0.5
+CLAMP = 1  # HJ_CLAMP_MONOTONE
 
 # Algorithmic work per grid-point update (one node, one full TVD-RK3 step),
 # counted from the discrete operator (FMA = 2 flops, reciprocal = 1).
@@ -56,7 +57,7 @@ BYTES_PER_UPDATE = 32.0
 # DRAM bytes per stage launch (read + write, average of stages 1-3) from the
 # ncu capture summarised in profiles/stage_kernel_x41_weno5.md; set to None
 # whenever the stage kernel changes until it is captured again.
-STAGE_TRAFFIC_BYTES = (11.323904e6 + 22.627328e6 + 22.630656e6) / 3.0
+STAGE_TRAFFIC_BYTES = None
 # FP32 non-tensor peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
@@ -262,19 +263,20 @@ def main():
     # prior: converged value function of the previous (smaller) wind bound
     if args.profile_steps:
         g.set_disturbance_bound([-BOUND], [BOUND])
-        st = g.solve(hj.HJ_COLD, scheme=5, fixed_steps=args.profile_steps)
+        st = g.solve(hj.HJ_COLD, scheme=5, fixed_steps=args.profile_steps, clamp=CLAMP)
         torch.cuda.synchronize()
         print(json.dumps({"profile_steps": st["steps"], "dt": st["dt"]}))
         g.close()
         return
-    st_prior = g.solve(hj.HJ_COLD, scheme=5, max_steps=200000, max_wall_ms=120000.0, band=BAND)
+    st_prior = g.solve(hj.HJ_COLD, scheme=5, max_steps=200000, max_wall_ms=120000.0, band=BAND,
+                       clamp=CLAMP)
     assert st_prior["converged"], st_prior
     prior = torch.empty(npts, dtype=torch.float32, device="cuda")
     g.value_into(prior)
     g.set_disturbance_bound([-BOUND], [BOUND])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    cap = dict(scheme=5, max_steps=200000, max_wall_ms=120000.0, band=BAND)
+    cap = dict(scheme=5, max_steps=200000, max_wall_ms=120000.0, band=BAND, clamp=CLAMP)
 
     def step():
         c = g.solve(hj.HJ_COLD, **cap)
@@ -324,7 +326,7 @@ def main():
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    g.solve(hj.HJ_WARM, scheme=5, fixed_steps=kpass)
+    g.solve(hj.HJ_WARM, scheme=5, fixed_steps=kpass, clamp=CLAMP)
     e1.record(stream)
     e1.synchronize()
     per_launch_s = e0.elapsed_time(e1) / 1e3 / (3 * kpass)
@@ -383,7 +385,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": "x4_41^4_weno5_cold+warm_update", "grid": [N_AXIS] * 4,
                    "scheme": "WENO5", "rk": "TVD-RK3", "cfl": 0.5, "tol": 1e-4,
-                   "check_dt": 0.1, "stop_band": BAND, "wind_prior": BOUND_PRIOR, "wind": BOUND,
+                   "check_dt": 0.1, "stop_band": BAND, "clamp": "monotone", "wind_prior": BOUND_PRIOR, "wind": BOUND,
                    "l2": "flushed between timed steps", "parallelism": "independent grids per rank"},
         "latency_ms": {
             "cold_p50": float(np.percentile(cold_ms, 50)), "cold_p99": float(np.percentile(cold_ms, 99)),

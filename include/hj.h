@@ -207,6 +207,83 @@ hj_status hj_query_gradient(hj_grid g, int npts, const double* x, double* grad_o
  * the device by a max-reduction.  alpha_out has ndim entries. */
 hj_status hj_alpha(hj_grid g, double* alpha_out);
 
+/* ------------------------------------------------------------------ server
+ * Safety-update serving (Sec. II-C, Sec. III).  New disturbance bounds
+ * arrive over time and each one triggers an update solve of one subsystem.
+ * The server runs these solves with continuous batching:
+ *   - Admission: a background worker admits queued requests in arrival
+ *     order, whenever active slots and the HBM budget allow.  A request that
+ *     does not fit is skipped for smaller later ones.
+ *   - Stepping: all admitted requests advance together, one fused launch per
+ *     RK stage (as hj_solve_batch), each with its own dt and stop test.
+ *     A request that arrives while others run joins at the next round
+ *     boundary.
+ *   - Residency: each subsystem key keeps its latest converged value on the
+ *     device.  A later HJ_WARM request with the same key warm-starts from it
+ *     (Sec. III-B) only when the prior provably dominates the new fixed
+ *     point.  That needs the same grid and model, every disturbance
+ *     interval of the prior inside the new one, and the prior's constraint
+ *     box containing the new one.  Otherwise the request solves cold.
+ *   - Memory: results stay on the device until hj_server_release.  Released
+ *     results that are still a key's resident prior are evicted (least
+ *     recently used first) when the budget is needed.
+ * Handles are thread-safe: any host thread may submit, poll or wait. */
+typedef struct hj_server_s* hj_server;
+
+typedef struct {
+  int ndim;
+  int n[HJ_MAX_DIM];
+  double lo[HJ_MAX_DIM], hi[HJ_MAX_DIM];
+  int model;
+  double params[8];
+  int nparams;
+  double d_lo[HJ_MAX_DIM], d_hi[HJ_MAX_DIM];
+  int nd;
+  int con_ball;                 /* 0: box con_a = lo, con_b = hi; 1: ball, centre con_a, radius con_b[0] */
+  double con_a[HJ_MAX_DIM], con_b[HJ_MAX_DIM];
+  int mode;                     /* HJ_COLD, or HJ_WARM = use the key's resident prior when exact */
+  long long key;                /* subsystem identity for residency; 0 = none                  */
+  hj_solve_opts opts;
+} hj_request;
+
+typedef struct {
+  long long submitted, admitted, completed, failed, rejected;
+  long long warm_starts, cold_starts, evictions, rounds;
+  long long bytes_in_use, peak_bytes;
+  long long active;             /* requests stepping right now                                 */
+  long long queued;
+  double p50_ms, p99_ms;        /* submit-to-completion latency of completed requests          */
+  double updates;               /* grid-point updates (nodes x steps) of all finished requests */
+  double busy_ms;               /* wall time from first submit to last completion              */
+} hj_server_stats;
+
+/* Start a server on the current device.  hbm_budget_bytes bounds the device
+ * memory of all its grids (four FP32 fields per node).  max_active bounds
+ * the concurrent solves (<= 1024).  cuda_stream is the stream all work runs
+ * on (NULL = a private stream). */
+hj_status hj_server_create(hj_server* out, long long hbm_budget_bytes, int max_active,
+                           void* cuda_stream);
+/* Stop admitting, finish running requests, free everything. */
+void hj_server_destroy(hj_server s);
+/* Queue a request; *ticket identifies it.  The request is copied.
+ * HJ_ERR_ARG: bad request.  HJ_ERR_OOM: it can never fit the budget. */
+hj_status hj_server_submit(hj_server s, const hj_request* r, long long* ticket);
+/* *done = 1 once the request finished; then *result is its hj_solve status and
+ * *st its statistics (wall_ms = submit-to-completion latency). */
+hj_status hj_server_poll(hj_server s, long long ticket, int* done, hj_status* result,
+                         hj_solve_stats* st);
+/* Block until the request finished or timeout_ms passed (<= 0: no limit).
+ * HJ_ERR_NOT_CONVERGED is returned on timeout, HJ_OK when finished. */
+hj_status hj_server_wait(hj_server s, long long ticket, double timeout_ms, hj_status* result,
+                         hj_solve_stats* st);
+/* Copy a finished request's value function (dense row-major FP32) out. */
+hj_status hj_server_get_value(hj_server s, long long ticket, float* dst, int on_device);
+/* Drop the caller's interest in a ticket; its memory may then be reused. */
+hj_status hj_server_release(hj_server s, long long ticket);
+/* Cancel a queued or running request (it finishes with HJ_ERR_ABORTED). */
+hj_status hj_server_cancel(hj_server s, long long ticket);
+hj_status hj_server_get_stats(hj_server s, hj_server_stats* out);
+
 /* Allocation-free fixed-horizon solve.  The paper has no counterpart: this
  * entry point exists for callers that must not allocate device memory after
  * start-up.  One example is a real-time safety filter running beside a

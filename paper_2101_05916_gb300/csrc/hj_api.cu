@@ -42,7 +42,17 @@ hjd::DevGrid devgrid(const hj_grid g) {
     s *= g->n[i];
   }
   d.npts = (int)g->npts;
-  d.plane = g->ndim >= 2 ? g->n[g->ndim - 2] * g->n[g->ndim - 1] : g->n[0];
+  d.plane = g->ndim == 4 ? (int)(g->npts / g->n[0]) : (int)g->npts;
+  // multiply-shift reciprocals of the two fastest axis lengths (see fast_div)
+  for (int k = 0; k < 2; ++k) {
+    int ax = g->ndim - 1 - k;
+    unsigned dv = ax >= 0 ? (unsigned)g->n[ax] : 2u;
+    int l = 0;
+    while ((1ull << l) < dv) ++l;
+    unsigned long long num = 1ull << (31 + l);
+    d.div_m[k] = (unsigned)((num + dv - 1) / dv);
+    d.div_s[k] = l - 1;
+  }
   for (int i = 0; i < g->ndim; ++i) {
     d.lo[i] = (float)g->lo[i];
     d.h[i] = (float)g->h[i];
@@ -50,7 +60,13 @@ hjd::DevGrid devgrid(const hj_grid g) {
     d.h_d[i] = g->h[i];
     d.ih[i] = (float)(1.0 / g->h[i]);
     d.ih6[i] = (float)(1.0 / (6.0 * g->h[i]));
-    d.wfloor[i] = (float)(1e-18 * g->h[i] * g->h[i]);
+    // WENO epsilon floor: 1e-18 in divided differences, on undivided ones
+    // times h^2, times the 12/13 scale of the smoothness indicators
+    d.wfloor[i] = (float)(12.0 / 13.0 * 1e-18 * g->h[i] * g->h[i]);
+    d.hih[i] = (float)(0.5 / g->h[i]);
+    d.hih6[i] = (float)(0.5 / (6.0 * g->h[i]));
+    d.haih[i] = (float)(0.5 * (double)g->alpha[i] / g->h[i]);
+    d.haih6[i] = (float)(0.5 * (double)g->alpha[i] / (6.0 * g->h[i]));
   }
   d.model = g->model;
   for (int i = 0; i < 8; ++i) d.prm[i] = (float)g->params[i];

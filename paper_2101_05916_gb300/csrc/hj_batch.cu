@@ -2,10 +2,13 @@
 // x, y and z blocks of the 10-D quadcopter are independent problems, and the
 // paper runs them in parallel).
 //
-// Each TVD-RK3 stage of every active grid is ONE launch: a block first finds
-// its grid (binary search over block offsets), copies that grid's descriptor
-// into shared memory, and then runs the same per-node stage code as the
-// single-grid kernel.  After stage 3, a one-block control kernel advances
+// Each TVD-RK3 stage is ONE launch per grid kind (model, ndim, scheme) over
+// the blocks of all active grids of that kind.  Within a launch, a block first
+// finds its grid (binary search over block offsets), copies that grid's
+// descriptor into shared memory, and then runs the same per-node stage code
+// as the single-grid kernel.  Each kind is compiled separately, so it keeps
+// the register use of the single-grid kernel.  After stage 3, a one-block
+// control kernel advances
 // every grid's step counter.  It also closes check windows (residual vs.
 // tol) and clears the `active` flag of grids that converged, hit their cap or
 // went non-finite.  So all stop decisions happen on the device, and a round
@@ -28,26 +31,6 @@ __host__ __device__ constexpr int kind_code(int model, int ndim, int scheme) {
   return model * 100 + ndim * 10 + scheme;
 }
 
-template <int STAGE>
-__device__ __forceinline__ unsigned dispatch(const Item& it, int q, int yb, int zb, bool check) {
-  const hjd::DevGrid& g = it.g;
-  const hjd::StageArgs& a = it.a[STAGE - 1];
-  using namespace hjd;
-  switch (it.kind) {
-    case kind_code(M_QUAD_Z, 2, 1): return stage_point<2, 1, M_QUAD_Z, STAGE>(g, a, q, yb, zb, check);
-    case kind_code(M_QUAD_Z, 2, 2): return stage_point<2, 2, M_QUAD_Z, STAGE>(g, a, q, yb, zb, check);
-    case kind_code(M_QUAD_Z, 2, 5): return stage_point<2, 5, M_QUAD_Z, STAGE>(g, a, q, yb, zb, check);
-    case kind_code(M_QUAD_X4, 4, 1): return stage_point<4, 1, M_QUAD_X4, STAGE>(g, a, q, yb, zb, check);
-    case kind_code(M_QUAD_X4, 4, 2): return stage_point<4, 2, M_QUAD_X4, STAGE>(g, a, q, yb, zb, check);
-    case kind_code(M_QUAD_X4, 4, 5): return stage_point<4, 5, M_QUAD_X4, STAGE>(g, a, q, yb, zb, check);
-    case kind_code(M_DRIFT, 1, 2): return stage_point<1, 2, M_DRIFT, STAGE>(g, a, q, yb, zb, check);
-    case kind_code(M_DRIFT, 1, 5): return stage_point<1, 5, M_DRIFT, STAGE>(g, a, q, yb, zb, check);
-    case kind_code(M_DRIFT, 2, 2): return stage_point<2, 2, M_DRIFT, STAGE>(g, a, q, yb, zb, check);
-    case kind_code(M_DRIFT, 2, 5): return stage_point<2, 5, M_DRIFT, STAGE>(g, a, q, yb, zb, check);
-    default: return 0u;
-  }
-}
-
 static bool batch_supported(int model, int ndim, int scheme) {
   if (model == hjd::M_QUAD_Z) return ndim == 2;
   if (model == hjd::M_QUAD_X4) return ndim == 4;
@@ -55,45 +38,67 @@ static bool batch_supported(int model, int ndim, int scheme) {
   return false;
 }
 
-template <int STAGE>
-__global__ void __launch_bounds__(kThreads) batch_stage(const Item* __restrict__ items, int nitems,
+// One fused launch for up to kPackItems active grids of one kind (model,
+// ndim, scheme).  It is compiled for that single variant, so its register use
+// matches the single-grid kernel.  The descriptors arrive as a
+// __grid_constant__ parameter and are indexed by a block-uniform value, so
+// their fields are constant-bank reads, as in the single-grid kernel.
+template <int STAGE, int D, int S, int M>
+__global__ void __launch_bounds__(kThreads) batch_stage(const __grid_constant__ ItemPack pack,
                                                          Ctl* ctl) {
-  __shared__ Item it;
-  __shared__ int k_s;
-  if (threadIdx.x == 0) {
-    int lo = 0, hi = nitems - 1;
-    while (lo < hi) {
-      int mid = (lo + hi + 1) >> 1;
-      if (items[mid].block_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
-    }
-    k_s = lo;
+  int lo = 0, hi = pack.count - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (pack.block_begin[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
   }
-  __syncthreads();
-  {
-    const int* src = reinterpret_cast<const int*>(items + k_s);
-    int* dst = reinterpret_cast<int*>(&it);
-    for (int i = threadIdx.x; i < (int)(sizeof(Item) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
-  }
-  __syncthreads();
+  const Item& it = pack.items[lo];
   const Ctl& c = ctl[it.slot];
   if (!c.active) return;  // uniform: written only by the control kernel
-  int lb = blockIdx.x - it.block_begin;
-  int bxi = lb % it.bx;
-  int rest = lb / it.bx;
-  int yb = rest % it.by;
-  int zb = rest / it.by;
+  int lb = blockIdx.x - pack.block_begin[lo];
+  int yb = lb / it.bx;
+  int bxi = lb - yb * it.bx;
   bool check = false;
   if (STAGE == 3) {
     long long s1 = c.steps + 1;
     check = (s1 % c.per == 0) || (s1 >= c.max_steps);
   }
-  unsigned r = dispatch<STAGE>(it, bxi * kThreads + threadIdx.x, yb, zb, check);
+  unsigned r = hjd::stage_point<D, S, M, STAGE>(it.g, it.a[STAGE - 1], bxi * kThreads + threadIdx.x,
+                                                yb, check);
   if (STAGE == 3 && check) hjd::block_max_bits(r, &ctl[it.slot].resid);
 }
 
-__global__ void batch_control(const Item* __restrict__ items, int nitems, Ctl* ctl) {
+// One stage launch of one pack; false for a kind without a kernel.
+static bool launch_kind(int kind, const ItemPack& pack, int blocks, Ctl* ctl, cudaStream_t s,
+                        int stage) {
+  using namespace hjd;
+  auto go = [&](auto k1, auto k2, auto k3) {
+    if (stage == 1) k1<<<blocks, kThreads, 0, s>>>(pack, ctl);
+    else if (stage == 2) k2<<<blocks, kThreads, 0, s>>>(pack, ctl);
+    else k3<<<blocks, kThreads, 0, s>>>(pack, ctl);
+  };
+#define HJ_KIND(MODEL, D, S)                                                              \
+  case kind_code(MODEL, D, S):                                                            \
+    go(batch_stage<1, D, S, MODEL>, batch_stage<2, D, S, MODEL>, batch_stage<3, D, S, MODEL>); \
+    return true;
+  switch (kind) {
+    HJ_KIND(M_QUAD_Z, 2, 1)
+    HJ_KIND(M_QUAD_Z, 2, 2)
+    HJ_KIND(M_QUAD_Z, 2, 5)
+    HJ_KIND(M_QUAD_X4, 4, 1)
+    HJ_KIND(M_QUAD_X4, 4, 2)
+    HJ_KIND(M_QUAD_X4, 4, 5)
+    HJ_KIND(M_DRIFT, 1, 2)
+    HJ_KIND(M_DRIFT, 1, 5)
+    HJ_KIND(M_DRIFT, 2, 2)
+    HJ_KIND(M_DRIFT, 2, 5)
+    default: return false;
+  }
+#undef HJ_KIND
+}
+
+__global__ void batch_control(const int* __restrict__ slots, int nitems, Ctl* ctl) {
   for (int k = threadIdx.x; k < nitems; k += blockDim.x) {
-    Ctl& c = ctl[items[k].slot];
+    Ctl& c = ctl[slots[k]];
     if (!c.active) continue;
     long long s = ++c.steps;
     if (s % c.per == 0 || s >= c.max_steps) {
@@ -125,7 +130,7 @@ Runner::~Runner() {
   cudaStreamSynchronize(stream_);
   drop_graphs();
   cudaFree(dev_ctl_);
-  cudaFree(dev_items_);
+  cudaFree(dev_slots_);
   if (host_ctl_) cudaFreeHost(host_ctl_);
   if (cap_stream_) cudaStreamDestroy(cap_stream_);
 }
@@ -236,40 +241,58 @@ hj_status Runner::cancel(int k) {
 }
 
 hj_status Runner::rebuild() {
-  std::vector<Item> items;
   order_.clear();
-  int begin = 0;
+  groups_.clear();
+  // grids of one kind share fused launches of up to kPackItems grids each
+  std::vector<std::pair<int, int>> by_kind;  // (kind, slot)
   for (int k = 0; k < cap_; ++k) {
     Slot& s = slots_[k];
     if (!s.used || s.done) continue;
+    by_kind.emplace_back(kind_code(s.g->model, s.g->ndim, s.scheme), k);
+  }
+  std::stable_sort(by_kind.begin(), by_kind.end(),
+                   [](const std::pair<int, int>& a, const std::pair<int, int>& b) {
+                     return a.first < b.first;
+                   });
+  for (size_t j = 0; j < by_kind.size(); ++j) {
+    int k = by_kind[j].second;
+    Slot& s = slots_[k];
     hj_grid g = s.g;
-    Item it;
-    std::memset(&it, 0, sizeof(it));
+    if (groups_.empty() || groups_.back().kind != by_kind[j].first ||
+        groups_.back().pack.count == kPackItems) {
+      groups_.emplace_back();
+      Group& ng = groups_.back();
+      std::memset(&ng.pack, 0, sizeof(ng.pack));
+      ng.kind = by_kind[j].first;
+      ng.blocks = 0;
+    }
+    Group& gr = groups_.back();
+    Item& it = gr.pack.items[gr.pack.count];
     it.g = hja::devgrid(g);
     float dt = (float)s.dt;
     it.a[0] = hjd::StageArgs{g->W, g->W, g->A, nullptr, nullptr, dt, 0, s.clamp, s.band};
     it.a[1] = hjd::StageArgs{g->A, g->W, g->B, nullptr, nullptr, dt, 0, s.clamp, s.band};
     it.a[2] = hjd::StageArgs{g->B, g->W, g->W, g->snap, nullptr, dt, 1, s.clamp, s.band};
-    it.kind = kind_code(g->model, g->ndim, s.scheme);
+    it.kind = by_kind[j].first;
     it.slot = k;
     it.bx = (it.g.plane + kThreads - 1) / kThreads;
-    it.by = g->ndim >= 3 ? g->n[g->ndim - 3] : 1;
-    int bz = g->ndim == 4 ? g->n[0] : 1;
-    it.block_begin = begin;
-    begin += it.bx * it.by * bz;
-    items.push_back(it);
+    it.by = g->ndim == 4 ? g->n[0] : 1;
+    it.block_begin = gr.blocks;
+    gr.pack.block_begin[gr.pack.count] = gr.blocks;
+    gr.blocks += it.bx * it.by;
+    gr.pack.count += 1;
+    gr.pack.block_begin[gr.pack.count] = gr.blocks;
     order_.push_back(k);
   }
-  nitems_ = (int)items.size();
-  total_blocks_ = begin;
+  nitems_ = (int)order_.size();
   if (nitems_ > item_cap_) {
-    cudaFree(dev_items_);
-    dev_items_ = nullptr;
+    cudaFree(dev_slots_);
+    dev_slots_ = nullptr;
     item_cap_ = std::max(nitems_, 2 * item_cap_);
-    HJ_CU(cudaMalloc(&dev_items_, sizeof(Item) * item_cap_));
+    HJ_CU(cudaMalloc(&dev_slots_, sizeof(int) * item_cap_));
   }
   if (nitems_) {
-    HJ_CU(cudaMemcpyAsync(dev_items_, items.data(), sizeof(Item) * nitems_, cudaMemcpyHostToDevice,
+    HJ_CU(cudaMemcpyAsync(dev_slots_, order_.data(), sizeof(int) * nitems_, cudaMemcpyHostToDevice,
                           stream_));
     HJ_CU(cudaStreamSynchronize(stream_));
   }
@@ -278,13 +301,15 @@ hj_status Runner::rebuild() {
   return HJ_OK;
 }
 
-static cudaError_t enqueue_round(const Item* items, int nitems, int blocks, Ctl* ctl, long long R,
-                                 cudaStream_t s) {
+// R steps: per step, the three stage launches of every kind group, then the
+// control kernel over all grids.
+cudaError_t Runner::enqueue_round(long long R, cudaStream_t s) {
   for (long long i = 0; i < R; ++i) {
-    batch_stage<1><<<blocks, kThreads, 0, s>>>(items, nitems, ctl);
-    batch_stage<2><<<blocks, kThreads, 0, s>>>(items, nitems, ctl);
-    batch_stage<3><<<blocks, kThreads, 0, s>>>(items, nitems, ctl);
-    batch_control<<<1, 256, 0, s>>>(items, nitems, ctl);
+    for (int stage = 1; stage <= 3; ++stage)
+      for (const Group& gr : groups_)
+        if (!launch_kind(gr.kind, gr.pack, gr.blocks, dev_ctl_, s, stage))
+          return cudaErrorInvalidValue;
+    batch_control<<<1, 256, 0, s>>>(dev_slots_, nitems_, dev_ctl_);
   }
   return cudaGetLastError();
 }
@@ -308,8 +333,12 @@ hj_status Runner::sync_ctl() {
 hj_status Runner::round(bool use_graph) {
   hja::DeviceGuard dg(device_);
   hj_status st;
+  bool changed = dirty_;
   if (dirty_ && (st = rebuild()) != HJ_OK) return st;
   if (nitems_ == 0) return HJ_OK;
+  // capture only a membership that repeats: a fresh set runs its first round
+  // with direct launches
+  use_graph = use_graph && !changed;
   // run to the next window boundary of any active grid
   long long R = 1ll << 62;
   for (int k : order_) {
@@ -324,7 +353,7 @@ hj_status Runner::round(bool use_graph) {
     if (it == graphs_.end()) {
       cudaGraph_t graph = nullptr;
       HJ_CU(cudaStreamBeginCapture(cap_stream_, cudaStreamCaptureModeThreadLocal));
-      cudaError_t e = enqueue_round(dev_items_, nitems_, total_blocks_, dev_ctl_, R, cap_stream_);
+      cudaError_t e = enqueue_round(R, cap_stream_);
       cudaError_t e2 = cudaStreamEndCapture(cap_stream_, &graph);
       if (e != cudaSuccess || e2 != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);
@@ -339,9 +368,9 @@ hj_status Runner::round(bool use_graph) {
     }
     HJ_CU(cudaGraphLaunch(it->second, stream_));
   } else {
-    HJ_CU(enqueue_round(dev_items_, nitems_, total_blocks_, dev_ctl_, R, stream_));
+    HJ_CU(enqueue_round(R, stream_));
   }
-  hjk::g_launches.fetch_add(4ull * (unsigned long long)R);
+  hjk::g_launches.fetch_add((3ull * groups_.size() + 1ull) * (unsigned long long)R);
   if ((st = sync_ctl()) != HJ_OK) return st;
   // wall-time caps are host-side and apply between rounds
   auto now = std::chrono::steady_clock::now();

@@ -16,8 +16,20 @@ struct Item {
   int kind;             // model * 100 + ndim * 10 + scheme
   int slot;             // index into the control array
   int block_begin;      // first block of this grid in the fused launch
-  int bx, by;           // plane blocks; slabs along axis ndim-3
+  int bx, by;           // blocks per slab; slabs (first-axis nodes of a 4-D grid, else 1)
 };
+
+// Grids of one fused launch, passed as a __grid_constant__ kernel parameter.
+// A block finds its grid from the block offsets.  Every later descriptor
+// read is then a uniform constant-bank load, as in the single-grid kernel,
+// rather than a shared-memory load per use.
+constexpr int kPackItems = 24;
+struct ItemPack {
+  int count;
+  int block_begin[kPackItems + 1];
+  Item items[kPackItems];
+};
+static_assert(sizeof(ItemPack) <= 32000, "kernel parameters are limited to 32764 bytes");
 
 // Per-grid stepping state, written only by the control kernel between steps.
 struct Ctl {
@@ -35,8 +47,9 @@ struct Ctl {
 enum { S_RUNNING = 0, S_CONVERGED = 1, S_CAP = 2, S_NONFINITE = 3, S_CANCELLED = 4 };
 
 // Steps a changing set of grids together.  Grids join with add() and leave
-// when their control state says so; every round advances all active grids by
-// the same number of steps in one fused launch per RK stage.
+// when their control state says so.  Every round advances all active grids by
+// the same number of steps.  Each step is one fused launch per RK stage and
+// per grid kind (model, ndim, scheme), plus one control launch.
 class Runner {
  public:
   Runner(int device, cudaStream_t stream, int capacity = 1024);
@@ -65,9 +78,15 @@ class Runner {
     std::chrono::steady_clock::time_point t0;
     double wall_ms = 0.0;
   };
+  struct Group {
+    int kind;      // model * 100 + ndim * 10 + scheme
+    ItemPack pack; // up to kPackItems grids of that kind
+    int blocks;    // blocks of one fused stage launch over the pack
+  };
   hj_status rebuild();
   hj_status sync_ctl();
   void drop_graphs();
+  cudaError_t enqueue_round(long long R, cudaStream_t s);
 
   int device_;
   cudaStream_t stream_;
@@ -75,10 +94,10 @@ class Runner {
   std::vector<Slot> slots_;
   Ctl* dev_ctl_ = nullptr;
   Ctl* host_ctl_ = nullptr;  // pinned mirror
-  Item* dev_items_ = nullptr;
+  int* dev_slots_ = nullptr;   // control slots of the current items, in launch order
   int item_cap_ = 0;
   int nitems_ = 0;
-  int total_blocks_ = 0;
+  std::vector<Group> groups_;
   bool dirty_ = true;
   std::vector<int> order_;  // slots in the current item list
   std::map<long long, cudaGraphExec_t> graphs_;  // round length -> graph

@@ -29,13 +29,20 @@ struct DevGrid {
   int n[MAXD];
   int stride[MAXD];    // row-major, last axis fastest
   int npts;
-  int plane;           // nodes in the flattened last-two-axes plane (all nodes if ndim <= 2)
+  int plane;           // nodes of one thread slab: all axes but the first of a 4-D grid,
+                       // every node of a grid with ndim <= 3
+  unsigned div_m[2];   // n[ndim-1], n[ndim-2] as multiply-shift reciprocals
+  int div_s[2];
   float lo[MAXD];
   float h[MAXD];
   double lo_d[MAXD];   // the same box in double, for interpolation
   double h_d[MAXD];
   float ih[MAXD];      // 1 / h
   float ih6[MAXD];     // 1 / (6 h), folds the 1/6 of the WENO candidates
+  float hih[MAXD];     // 0.5 / h        (first order, ENO2)
+  float hih6[MAXD];    // 0.5 / (6 h)    (WENO5)
+  float haih[MAXD];    // 0.5 a / h
+  float haih6[MAXD];   // 0.5 a / (6 h)
   float wfloor[MAXD];  // WENO epsilon floor on undivided differences: 1e-18 h^2
   int model;
   float prm[8];
@@ -64,6 +71,14 @@ __device__ __forceinline__ float rcp_approx(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
+}
+
+// Quotient of q < 2^31 by the divisor encoded as (m, s) with s = ceil(log2 d) - 1
+// and m = ceil(2^(31 + s + 1) / d): floor(q m / 2^(32 + s)).  For divisors
+// d >= 2 the rounding error q (m - 2^(32+s)/d) / 2^(32+s) < 1/d never crosses
+// an integer.
+__device__ __forceinline__ int fast_div(int q, unsigned m, int s) {
+  return (int)(__umulhi((unsigned)q, m) >> s);
 }
 
 // ---------------------------------------------------------------- geometry
@@ -198,51 +213,87 @@ __device__ __forceinline__ void load_line(const float* __restrict__ src, int p, 
 
 // ------------------------------------------------------------- slopes
 
-// WENO5 of Jiang & Peng on undivided differences q1..q5 in upwind order.
-// Returns 6 * h * slope (the caller multiplies by 1 / (6 h)).
+// Both one-sided WENO5 slopes (Jiang & Peng) at a node, from the six
+// undivided differences D_k = v[k+1] - v[k] of the line values v at offsets
+// -3..3.  The left-biased slope uses D0..D4; the right-biased slope uses
+// D5..D1 in upwind order.  Returns 6 h p- and 6 h p+; the caller folds in
+// 1 / (6 h).
 //
-// The nonlinear weights a_k = c_k / (S_k + eps)^2 are normalised, so any
-// common factor cancels.  Multiplying every S_k + eps by 1 / eps and then
-// every a_k by the product of all three squares gives weights
-// c_1 s_2^2 s_3^2, c_2 s_1^2 s_3^2, c_3 s_1^2 s_2^2 with s_k = S_k / eps + 1.
-// Since S_k <= 34 max q^2 and eps >= 1e-6 max q^2, every s_k lies in
-// [1, 3.4e7], so these products stay inside FP32 range.  The rewrite needs
-// two reciprocals instead of four.
-__device__ __forceinline__ float weno5_6h(float q1, float q2, float q3, float q4, float q5,
-                                          float floor_) {
-  const float k1312 = 13.f / 12.f;
-  float t1 = fmaf(-2.f, q2, q1 + q3);
-  float u1 = fmaf(3.f, q3, fmaf(-4.f, q2, q1));
-  float t2 = fmaf(-2.f, q3, q2 + q4);
-  float u2 = q2 - q4;
-  float t3 = fmaf(-2.f, q4, q3 + q5);
-  float u3 = fmaf(3.f, q3, fmaf(-4.f, q4, q5));
-  float S1 = fmaf(k1312 * t1, t1, 0.25f * u1 * u1);
-  float S2 = fmaf(k1312 * t2, t2, 0.25f * u2 * u2);
-  float S3 = fmaf(k1312 * t3, t3, 0.25f * u3 * u3);
-  float m = fmaxf(fmaxf(fmaxf(fabsf(q1), fabsf(q2)), fmaxf(fabsf(q3), fabsf(q4))), fabsf(q5));
-  float ie = rcp_approx(fmaf(1e-6f * m, m, floor_));
-  float s1 = fmaf(S1, ie, 1.f), s2 = fmaf(S2, ie, 1.f), s3 = fmaf(S3, ie, 1.f);
-  float a1 = s1 * s1, a2 = s2 * s2, a3 = s3 * s3;
-  float w1 = 0.1f * (a2 * a3), w2 = 0.6f * (a1 * a3), w3 = 0.3f * (a1 * a2);
-  float phi1 = fmaf(2.f, q1, fmaf(-7.f, q2, 11.f * q3));
-  float phi2 = fmaf(5.f, q3, fmaf(2.f, q4, -q2));
-  float phi3 = fmaf(2.f, q3, fmaf(5.f, q4, -q5));
-  float num = fmaf(w1, phi1, fmaf(w2, phi2, w3 * phi3));
-  return num * rcp_approx(w1 + w2 + w3);
+// The arithmetic is the textbook scheme, rearranged to save instructions:
+//   - Second differences t and the max |D| are shared by the two sides.
+//   - Each smoothness indicator 13/12 t^2 + 1/4 u^2 is computed as
+//     t^2 + (3/13) u^2, i.e. scaled by 12/13.  The epsilon is scaled by the
+//     same factor, so every S_k + eps changes by one common factor, which
+//     normalised weights cancel.
+//   - Nonlinear weights a_k = c_k / (S_k + eps)^2 are evaluated as
+//     c_1 s_2^2 s_3^2, c_2 s_1^2 s_3^2, c_3 s_1^2 s_2^2 with
+//     s_k = S_k / eps + 1.  That is the same normalised set, multiplied
+//     through by a common factor.  Since S_k <= 34 max D^2 and
+//     eps >= 1e-6 max D^2, every s_k lies in [1, 3.4e7], so the products
+//     stay inside FP32 range.  It takes one reciprocal per weight set.
+//   - The linear weights (1/10, 6/10, 3/10) are folded into the candidate
+//     coefficients.
+__device__ __forceinline__ void weno5_pair(float D0, float D1, float D2, float D3, float D4,
+                                           float D5, float floor_, float& pm6h, float& pp6h) {
+  const float k = 0.48038446141526137f;  // sqrt(3/13)
+  // second differences of the four difference triples
+  float t0 = fmaf(-2.f, D1, D0 + D2);
+  float t1 = fmaf(-2.f, D2, D1 + D3);
+  float t2 = fmaf(-2.f, D3, D2 + D4);
+  float t3 = fmaf(-2.f, D4, D3 + D5);
+  // sqrt(3/13)-scaled first-difference combinations of each role
+  float uA0 = fmaf(3.f * k, D2, fmaf(-4.f * k, D1, k * D0));   // (D0,D1,D2), left end
+  float uB1 = fmaf(k, D1, -k * D3);                            // (D1,D2,D3), centre
+  float uC2 = fmaf(3.f * k, D2, fmaf(-4.f * k, D3, k * D4));   // (D2,D3,D4), right end
+  float uC3 = fmaf(3.f * k, D3, fmaf(-4.f * k, D4, k * D5));   // (D3,D4,D5), right end
+  float uB2 = fmaf(k, D2, -k * D4);                            // (D2,D3,D4), centre
+  float uA1 = fmaf(3.f * k, D3, fmaf(-4.f * k, D2, k * D1));   // (D1,D2,D3), left end
+  // smoothness indicators (scaled by 12/13)
+  float Sm1 = fmaf(t0, t0, uA0 * uA0), Sm2 = fmaf(t1, t1, uB1 * uB1), Sm3 = fmaf(t2, t2, uC2 * uC2);
+  float Sp1 = fmaf(t3, t3, uC3 * uC3), Sp2 = fmaf(t2, t2, uB2 * uB2), Sp3 = fmaf(t1, t1, uA1 * uA1);
+  // epsilon = 1e-6 max D^2 + floor, scaled by 12/13 like the indicators
+  float mid = fmaxf(fmaxf(fabsf(D1), fabsf(D2)), fmaxf(fabsf(D3), fabsf(D4)));
+  float mm = fmaxf(mid, fabsf(D0)), mp = fmaxf(mid, fabsf(D5));
+  const float e6 = 1e-6f * (12.f / 13.f);
+  float iem = rcp_approx(fmaf(e6 * mm, mm, floor_));
+  float iep = rcp_approx(fmaf(e6 * mp, mp, floor_));
+  float a1 = fmaf(Sm1, iem, 1.f), a2 = fmaf(Sm2, iem, 1.f), a3 = fmaf(Sm3, iem, 1.f);
+  float b1 = fmaf(Sp1, iep, 1.f), b2 = fmaf(Sp2, iep, 1.f), b3 = fmaf(Sp3, iep, 1.f);
+  a1 *= a1; a2 *= a2; a3 *= a3;
+  b1 *= b1; b2 *= b2; b3 *= b3;
+  float Pm1 = a2 * a3, Pm2 = a1 * a3, Pm3 = a1 * a2;
+  float Pp1 = b2 * b3, Pp2 = b1 * b3, Pp3 = b1 * b2;
+  // candidates times their linear weights
+  float cm1 = fmaf(0.2f, D0, fmaf(-0.7f, D1, 1.1f * D2));
+  float cm2 = fmaf(3.0f, D2, fmaf(1.2f, D3, -0.6f * D1));
+  float cm3 = fmaf(0.6f, D2, fmaf(1.5f, D3, -0.3f * D4));
+  float cp1 = fmaf(0.2f, D5, fmaf(-0.7f, D4, 1.1f * D3));
+  float cp2 = fmaf(3.0f, D3, fmaf(1.2f, D2, -0.6f * D4));
+  float cp3 = fmaf(0.6f, D3, fmaf(1.5f, D2, -0.3f * D1));
+  float numm = fmaf(Pm1, cm1, fmaf(Pm2, cm2, Pm3 * cm3));
+  float denm = fmaf(0.1f, Pm1, fmaf(0.6f, Pm2, 0.3f * Pm3));
+  float nump = fmaf(Pp1, cp1, fmaf(Pp2, cp2, Pp3 * cp3));
+  float denp = fmaf(0.1f, Pp1, fmaf(0.6f, Pp2, 0.3f * Pp3));
+  pm6h = numm * rcp_approx(denm);
+  pp6h = nump * rcp_approx(denp);
 }
 
+// Per scheme: the stencil radius R and raw one-sided slopes whose scale the
+// caller removes with folded per-axis constants (half and half-alpha times
+// 1/h for first order and ENO2, times 1/(6h) for WENO5).
 template <int S>
 struct Slopes;
 
 template <>
 struct Slopes<1> {
   static constexpr int R = 1;
-  __device__ __forceinline__ static void eval(const float (&v)[3], const DevGrid& g, int d,
+  __device__ __forceinline__ static void eval(const float (&v)[3], const DevGrid&, int,
                                               float& pm, float& pp) {
-    pm = (v[1] - v[0]) * g.ih[d];
-    pp = (v[2] - v[1]) * g.ih[d];
+    pm = v[1] - v[0];
+    pp = v[2] - v[1];
   }
+  __device__ __forceinline__ static float half(const DevGrid& g, int d) { return g.hih[d]; }
+  __device__ __forceinline__ static float half_alpha(const DevGrid& g, int d) { return g.haih[d]; }
 };
 
 // ENO2: first difference plus half the smaller (in magnitude) of the two
@@ -250,16 +301,18 @@ struct Slopes<1> {
 template <>
 struct Slopes<2> {
   static constexpr int R = 2;
-  __device__ __forceinline__ static void eval(const float (&v)[5], const DevGrid& g, int d,
+  __device__ __forceinline__ static void eval(const float (&v)[5], const DevGrid&, int,
                                               float& pm, float& pp) {
     float a = fmaf(-2.f, v[1], v[2] + v[0]);
     float b = fmaf(-2.f, v[2], v[3] + v[1]);
     float c = fmaf(-2.f, v[3], v[4] + v[2]);
     float m1 = (fabsf(a) <= fabsf(b)) ? a : b;
     float m2 = (fabsf(b) <= fabsf(c)) ? b : c;
-    pm = fmaf(0.5f, m1, v[2] - v[1]) * g.ih[d];
-    pp = fmaf(-0.5f, m2, v[3] - v[2]) * g.ih[d];
+    pm = fmaf(0.5f, m1, v[2] - v[1]);
+    pp = fmaf(-0.5f, m2, v[3] - v[2]);
   }
+  __device__ __forceinline__ static float half(const DevGrid& g, int d) { return g.hih[d]; }
+  __device__ __forceinline__ static float half_alpha(const DevGrid& g, int d) { return g.haih[d]; }
 };
 
 template <>
@@ -267,15 +320,16 @@ struct Slopes<5> {
   static constexpr int R = 3;
   __device__ __forceinline__ static void eval(const float (&v)[7], const DevGrid& g, int d,
                                               float& pm, float& pp) {
-    float D0 = v[1] - v[0], D1 = v[2] - v[1], D2 = v[3] - v[2];
-    float D3 = v[4] - v[3], D4 = v[5] - v[4], D5 = v[6] - v[5];
-    float f = g.wfloor[d];
-    pm = weno5_6h(D0, D1, D2, D3, D4, f) * g.ih6[d];
-    pp = weno5_6h(D5, D4, D3, D2, D1, f) * g.ih6[d];
+    weno5_pair(v[1] - v[0], v[2] - v[1], v[3] - v[2], v[4] - v[3], v[5] - v[4], v[6] - v[5],
+               g.wfloor[d], pm, pp);
   }
+  __device__ __forceinline__ static float half(const DevGrid& g, int d) { return g.hih6[d]; }
+  __device__ __forceinline__ static float half_alpha(const DevGrid& g, int d) { return g.haih6[d]; }
 };
 
 // L(src) at node p with multi-index idx; also returns src[p] in `center`.
+// The last axis is the fastest, so its stride is 1; its neighbours are then
+// immediate offsets of one address.
 template <int D, int S, int M>
 __device__ __forceinline__ float lf_rhs(const DevGrid& g, const float* __restrict__ src, int p,
                                         const int (&idx)[D], const float (&x)[D], float& center) {
@@ -285,12 +339,12 @@ __device__ __forceinline__ float lf_rhs(const DevGrid& g, const float* __restric
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     float v[2 * R + 1];
-    load_line<R>(src, p, g.stride[d], idx[d], g.n[d], v);
-    if (d == 0) center = v[R];
+    load_line<R>(src, p, d == D - 1 ? 1 : g.stride[d], idx[d], g.n[d], v);
+    if (d == D - 1) center = v[R];
     float pm, pp;
     Slopes<S>::eval(v, g, d, pm, pp);
-    pbar[d] = 0.5f * (pm + pp);
-    diss = fmaf(0.5f * g.alpha[d], pp - pm, diss);
+    pbar[d] = Slopes<S>::half(g, d) * (pm + pp);
+    diss = fmaf(Slopes<S>::half_alpha(g, d), pp - pm, diss);
   }
   return hamiltonian<M, D>(g, x, idx, pbar) + diss;
 }

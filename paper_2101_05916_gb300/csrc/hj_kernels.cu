@@ -9,12 +9,13 @@
 //  prolong_kernel coarse-to-fine migration (Sec. III-C).
 //  query_kernel   value / gradient read-out for the safety controller (Sec. II-A).
 //
-// The stencil is FP32-issue bound (about 500 FP32 instructions per node and
-// stage for WENO5 in 4-D against 8-12 bytes of compulsory traffic), so
-// threads map one-to-one onto nodes of the flattened last-two-axes plane.
-// That keeps warps fully populated whatever the axis lengths.  Line
-// neighbours come through the read-only (L1) path; warps of a block cover
-// adjacent rows, which makes the +-3 neighbours along the two fast axes L1
+// The stencil is bound by FP32 instruction issue: about 450 FP32
+// instructions per node and stage for WENO5 in 4-D, against 8-12 bytes of
+// compulsory traffic.  So threads map one-to-one onto nodes.  A 4-D grid runs
+// one slab of its last three axes per blockIdx.y; lower ranks are a single
+// slab.  That keeps warps fully populated whatever the axis lengths.  Line
+// neighbours come through the read-only (L1) path.  The warps of a block
+// cover adjacent rows, so the +-3 neighbours along the two fast axes are L1
 // hits.
 #include <algorithm>
 #include <cstdio>
@@ -32,7 +33,7 @@ using hjd::StageArgs;
 template <int D, int S, int M, int STAGE>
 __global__ void __launch_bounds__(kStageThreads) stage_kernel(const DevGrid g, const StageArgs a) {
   unsigned r = hjd::stage_point<D, S, M, STAGE>(g, a, blockIdx.x * blockDim.x + threadIdx.x,
-                                                blockIdx.y, blockIdx.z, a.check != 0);
+                                                blockIdx.y, a.check != 0);
   if constexpr (STAGE == 3) {
     if (a.check) hjd::block_max_bits(r, a.resid);
   }
@@ -191,9 +192,8 @@ __global__ void query_kernel(const DevGrid g, const float* __restrict__ W, int n
 
 static dim3 stage_grid(const DevGrid& g) {
   unsigned bx = (unsigned)((g.plane + kStageThreads - 1) / kStageThreads);
-  unsigned by = g.ndim >= 3 ? (unsigned)g.n[g.ndim - 3] : 1u;
-  unsigned bz = g.ndim == 4 ? (unsigned)g.n[0] : 1u;
-  return dim3(bx, by, bz);
+  unsigned by = g.ndim == 4 ? (unsigned)g.n[0] : 1u;
+  return dim3(bx, by, 1u);
 }
 
 template <int D, int S, int M>

@@ -6,32 +6,33 @@
 
 namespace hjd {
 
-// Node handled by plane index q in slab (yb, zb): the plane holds the last
-// two axes (all of them for ndim <= 2); yb indexes axis ndim-3 and zb axis 0
-// of a 4-D grid.
+// Node handled by thread index q of slab yb.  A 4-D grid runs one slab per
+// value of its first axis (yb), and q walks the other three axes.  A grid
+// with ndim <= 3 is one slab (yb = 0) holding every node.  Flattening three
+// axes keeps warps full whatever the axis lengths.  The divisions use
+// precomputed multiply-shift reciprocals.
 template <int D>
-__device__ __forceinline__ bool node_of(const DevGrid& g, int q, int yb, int zb, int (&idx)[D],
-                                        int& p) {
+__device__ __forceinline__ bool node_of(const DevGrid& g, int q, int yb, int (&idx)[D], int& p) {
   if constexpr (D == 1) {
     idx[0] = q;
     p = q;
-    return q < g.n[0];
   } else {
-    int inner = g.n[D - 1];
-    int a = q / inner;
-    idx[D - 2] = a;
-    idx[D - 1] = q - a * inner;
+    int a = fast_div(q, g.div_m[0], g.div_s[0]);
+    idx[D - 1] = q - a * g.n[D - 1];
+    if constexpr (D == 2) {
+      idx[0] = a;
+    } else {
+      int b = fast_div(a, g.div_m[1], g.div_s[1]);
+      idx[D - 2] = a - b * g.n[D - 2];
+      idx[D - 3] = b;
+    }
     p = q;
-    if constexpr (D >= 3) {
-      idx[D - 3] = yb;
-      p += yb * g.stride[D - 3];
-    }
     if constexpr (D == 4) {
-      idx[0] = zb;
-      p += zb * g.stride[0];
+      idx[0] = yb;
+      p += yb * g.stride[0];
     }
-    return q < g.plane;
   }
+  return q < g.plane;
 }
 
 template <int D>
@@ -40,7 +41,7 @@ __device__ __forceinline__ void coords(const DevGrid& g, const int (&idx)[D], fl
   for (int d = 0; d < D; ++d) x[d] = fmaf((float)idx[d], g.h[d], g.lo[d]);
 }
 
-// Stage STAGE of one TVD-RK3 step at the node of (q, yb, zb):
+// Stage STAGE of one TVD-RK3 step at the node of (q, yb):
 //   1: W1 = W + dt L(W)
 //   2: W2 = 3/4 W + 1/4 (W1 + dt L(W1))
 //   3: W3 = 1/3 W + 2/3 (W2 + dt L(W2)),  W <- min(W3, l)  [, W_prev]
@@ -48,10 +49,10 @@ __device__ __forceinline__ void coords(const DevGrid& g, const int (&idx)[D], fl
 // (stage 3 with check; 0 otherwise).
 template <int D, int S, int M, int STAGE>
 __device__ __forceinline__ unsigned stage_point(const DevGrid& g, const StageArgs& a, int q, int yb,
-                                                int zb, bool check) {
+                                                bool check) {
   int idx[D];
   int p;
-  if (!node_of<D>(g, q, yb, zb, idx, p)) return 0u;
+  if (!node_of<D>(g, q, yb, idx, p)) return 0u;
   float x[D];
   coords<D>(g, idx, x);
   float c;

@@ -61,6 +61,25 @@ class hj_solve_stats(ctypes.Structure):
 _P = ctypes.POINTER
 _vp, _i, _d, _ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
 
+
+class hj_request(ctypes.Structure):
+    _fields_ = [("ndim", _i), ("n", _i * HJ_MAX_DIM), ("lo", _d * HJ_MAX_DIM),
+                ("hi", _d * HJ_MAX_DIM), ("model", _i), ("params", _d * 8), ("nparams", _i),
+                ("d_lo", _d * HJ_MAX_DIM), ("d_hi", _d * HJ_MAX_DIM), ("nd", _i),
+                ("con_ball", _i), ("con_a", _d * HJ_MAX_DIM), ("con_b", _d * HJ_MAX_DIM),
+                ("mode", _i), ("key", _ll), ("opts", hj_solve_opts)]
+
+
+class hj_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", _ll), ("admitted", _ll), ("completed", _ll), ("failed", _ll),
+                ("rejected", _ll), ("warm_starts", _ll), ("cold_starts", _ll),
+                ("evictions", _ll), ("rounds", _ll), ("bytes_in_use", _ll),
+                ("peak_bytes", _ll), ("active", _ll), ("queued", _ll), ("p50_ms", _d),
+                ("p99_ms", _d), ("updates", _d), ("busy_ms", _d)]
+
+    def as_dict(self) -> Dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
 # C signatures: name -> (restype, argtypes)
 SIGNATURES = {
     "hj_default_opts": (None, [_P(hj_solve_opts)]),
@@ -83,6 +102,15 @@ SIGNATURES = {
     "hj_grid_points": (_ll, [_vp]),
     "hj_last_error": (ctypes.c_char_p, []),
     "hj_kernel_launches": (ctypes.c_ulonglong, []),
+    "hj_server_create": (_i, [_P(_vp), _ll, _i, _vp]),
+    "hj_server_destroy": (None, [_vp]),
+    "hj_server_submit": (_i, [_vp, _P(hj_request), _P(_ll)]),
+    "hj_server_poll": (_i, [_vp, _ll, _P(_i), _P(_i), _P(hj_solve_stats)]),
+    "hj_server_wait": (_i, [_vp, _ll, _d, _P(_i), _P(hj_solve_stats)]),
+    "hj_server_get_value": (_i, [_vp, _ll, _vp, _i]),
+    "hj_server_release": (_i, [_vp, _ll]),
+    "hj_server_cancel": (_i, [_vp, _ll]),
+    "hj_server_get_stats": (_i, [_vp, _P(hj_server_stats)]),
     "hj_solve_fixed_static": (_i, [_i, _P(_i), _P(_d), _P(_d), _i, _P(_d), _i, _P(_d), _P(_d),
                                    _i, _P(_d), _P(_d), _i, _i, _d, _ll, _i, _vp, _vp]),
 }
@@ -295,6 +323,87 @@ def hj_solve_fixed_static(spec, W, mode: int = HJ_COLD, scheme: int = HJ_WENO5,
                                        _darr(spec.con_b), int(mode), int(scheme), float(dt),
                                        int(steps), int(clamp), ptr, _stream_handle(stream)))
     del keep
+
+
+def make_request(spec, mode: int = HJ_COLD, key: int = 0, **opts) -> hj_request:
+    """An hj_request for a workloads.ProblemSpec."""
+    r = hj_request()
+    r.ndim = spec.ndim
+    for i in range(spec.ndim):
+        r.n[i] = int(spec.n[i])
+        r.lo[i] = float(spec.lo[i])
+        r.hi[i] = float(spec.hi[i])
+    r.model = MODELS[spec.model]
+    for i, v in enumerate(spec.params):
+        r.params[i] = float(v)
+    r.nparams = len(spec.params)
+    r.nd = len(spec.d_lo)
+    for i in range(r.nd):
+        r.d_lo[i] = float(spec.d_lo[i])
+        r.d_hi[i] = float(spec.d_hi[i])
+    r.con_ball = 0 if spec.con_kind == "box" else 1
+    for i, v in enumerate(spec.con_a):
+        r.con_a[i] = float(v)
+    for i, v in enumerate(spec.con_b):
+        r.con_b[i] = float(v)
+    r.mode = int(mode)
+    r.key = int(key)
+    r.opts = make_opts(**opts)
+    return r
+
+
+def hj_server_create(budget_bytes: int, max_active: int = 64, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().hj_server_create(ctypes.byref(h), int(budget_bytes), int(max_active),
+                                  _stream_handle(stream)))
+    return h.value
+
+
+def hj_server_destroy(s: int) -> None:
+    lib().hj_server_destroy(s)
+
+
+def hj_server_submit(s: int, req: hj_request) -> int:
+    t = ctypes.c_longlong()
+    _check(lib().hj_server_submit(s, ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def hj_server_poll(s: int, ticket: int):
+    """(done, status, stats dict)."""
+    done, res, st = ctypes.c_int(), ctypes.c_int(), hj_solve_stats()
+    _check(lib().hj_server_poll(s, ticket, ctypes.byref(done), ctypes.byref(res),
+                                ctypes.byref(st)))
+    return bool(done.value), res.value, st.as_dict()
+
+
+def hj_server_wait(s: int, ticket: int, timeout_ms: float = 0.0):
+    """(status, stats dict); raises HJError on timeout."""
+    res, st = ctypes.c_int(), hj_solve_stats()
+    _check(lib().hj_server_wait(s, ticket, float(timeout_ms), ctypes.byref(res),
+                                ctypes.byref(st)))
+    return res.value, st.as_dict()
+
+
+def hj_server_get_value(s: int, ticket: int, dst) -> None:
+    ptr, dev, keep = _field_ptr(dst, int(np.asarray(dst.shape).prod()) if hasattr(dst, "shape")
+                                else len(dst), True)
+    _check(lib().hj_server_get_value(s, ticket, ptr, dev))
+    del keep
+
+
+def hj_server_release(s: int, ticket: int) -> None:
+    _check(lib().hj_server_release(s, ticket))
+
+
+def hj_server_cancel(s: int, ticket: int) -> None:
+    _check(lib().hj_server_cancel(s, ticket))
+
+
+def hj_server_get_stats(s: int) -> Dict:
+    st = hj_server_stats()
+    _check(lib().hj_server_get_stats(s, ctypes.byref(st)))
+    return st.as_dict()
 
 
 def hj_grid_points(g: int) -> int:
