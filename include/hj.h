@@ -284,6 +284,21 @@ hj_status hj_server_release(hj_server s, long long ticket);
 hj_status hj_server_cancel(hj_server s, long long ticket);
 hj_status hj_server_get_stats(hj_server s, hj_server_stats* out);
 
+/* Admission policy.
+ *   order: HJ_ORDER_FIFO admits in arrival order (the default).
+ *     HJ_ORDER_SHORTEST admits the request with the least estimated work
+ *     first.  The estimate is nodes x the largest axis length, since the
+ *     steps to converge grow like 1 / dt ~ 1 / h.
+ *   max_active_nodes: if > 0, a request is admitted only while the nodes of
+ *     all stepping requests stay within it.  Exceptions: a request is always
+ *     admitted when nothing is stepping, and requests below 1/64 of the cap
+ *     are always admitted.  Large grids fill the GPU on their own; the cap
+ *     stops them from time-slicing each other, while small grids still run
+ *     beside them.
+ * Applies from the next admission on. */
+enum { HJ_ORDER_FIFO = 0, HJ_ORDER_SHORTEST = 1 };
+hj_status hj_server_set_policy(hj_server s, int order, long long max_active_nodes);
+
 /* Allocation-free fixed-horizon solve.  The paper has no counterpart: this
  * entry point exists for callers that must not allocate device memory after
  * start-up.  One example is a real-time safety filter running beside a

@@ -19,6 +19,7 @@
 #include <cfloat>
 #include <cmath>
 #include <cstring>
+#include <string>
 
 #include "hj_batch.h"
 #include "hj_stage.cuh"
@@ -302,13 +303,28 @@ hj_status Runner::rebuild() {
 }
 
 // R steps: per step, the three stage launches of every kind group, then the
-// control kernel over all grids.
+// control kernel over all grids.  A group holding a single grid uses the
+// single-grid kernel, whose descriptor is a plain kernel parameter.  Rounds
+// end at the first window boundary of any grid, so such a grid can check only
+// at the round's last step, and only when its own window ends there.
 cudaError_t Runner::enqueue_round(long long R, cudaStream_t s) {
   for (long long i = 0; i < R; ++i) {
-    for (int stage = 1; stage <= 3; ++stage)
-      for (const Group& gr : groups_)
-        if (!launch_kind(gr.kind, gr.pack, gr.blocks, dev_ctl_, s, stage))
+    for (int stage = 1; stage <= 3; ++stage) {
+      for (const Group& gr : groups_) {
+        if (gr.pack.count == 1) {
+          const Item& it = gr.pack.items[0];
+          hjd::StageArgs a = it.a[stage - 1];
+          const Ctl& c = host_ctl_[it.slot];
+          long long s1 = c.steps + i + 1;
+          a.check = (stage == 3 && (s1 % c.per == 0 || s1 >= c.max_steps)) ? 1 : 0;
+          a.resid = &dev_ctl_[it.slot].resid;
+          cudaError_t e = hjk::launch_stage(it.g, it.kind % 10, stage, a, s);
+          if (e != cudaSuccess) return e;
+        } else if (!launch_kind(gr.kind, gr.pack, gr.blocks, dev_ctl_, s, stage)) {
           return cudaErrorInvalidValue;
+        }
+      }
+    }
     batch_control<<<1, 256, 0, s>>>(dev_slots_, nitems_, dev_ctl_);
   }
   return cudaGetLastError();
@@ -347,9 +363,24 @@ hj_status Runner::round(bool use_graph) {
     long long to_cap = c.max_steps - c.steps;
     R = std::min(R, std::min(to_window, to_cap));
   }
-  R = std::max(1ll, std::min(R, 4096ll));
+  // bound a round to about 1e8 grid-point updates (a few ms) so that new
+  // arrivals join and finished grids leave promptly
+  long long active_nodes = 0;
+  for (int k : order_) active_nodes += slots_[k].g->npts;
+  long long r_work = std::max(16ll, 100000000ll / std::max(1ll, active_nodes));
+  R = std::max(1ll, std::min(R, std::min(r_work, 4096ll)));
+  // a single-grid group bakes its check step into the launch, so the graph
+  // key holds each such grid's phase within its window
+  std::string key = std::to_string(R);
+  for (const Group& gr : groups_)
+    if (gr.pack.count == 1) {
+      const Ctl& c = host_ctl_[gr.pack.items[0].slot];
+      long long to_cap = c.max_steps - c.steps;
+      key += "," + std::to_string(c.steps % c.per) + ":" + std::to_string(to_cap <= R ? to_cap : -1);
+    }
+  unsigned long long before = hjk::g_launches.load();
   if (use_graph) {
-    auto it = graphs_.find(R);
+    auto it = graphs_.find(key);
     if (it == graphs_.end()) {
       cudaGraph_t graph = nullptr;
       HJ_CU(cudaStreamBeginCapture(cap_stream_, cudaStreamCaptureModeThreadLocal));
@@ -364,13 +395,18 @@ hj_status Runner::round(bool use_graph) {
       cudaError_t e3 = cudaGraphInstantiate(&ex, graph, 0);
       cudaGraphDestroy(graph);
       if (e3 != cudaSuccess) return hja::fail(HJ_ERR_CUDA, "batch instantiate: %s", cudaGetErrorString(e3));
-      it = graphs_.emplace(R, ex).first;
+      if (graphs_.size() > 64) drop_graphs();
+      it = graphs_.emplace(key, ex).first;
     }
     HJ_CU(cudaGraphLaunch(it->second, stream_));
   } else {
     HJ_CU(enqueue_round(R, stream_));
   }
-  hjk::g_launches.fetch_add((3ull * groups_.size() + 1ull) * (unsigned long long)R);
+  // every kernel of the round counted once: single-grid launches counted
+  // themselves while enqueued (also during capture), so top up to the total
+  unsigned long long counted = hjk::g_launches.load() - before;
+  unsigned long long total = (3ull * groups_.size() + 1ull) * (unsigned long long)R;
+  if (total > counted) hjk::g_launches.fetch_add(total - counted);
   if ((st = sync_ctl()) != HJ_OK) return st;
   // wall-time caps are host-side and apply between rounds
   auto now = std::chrono::steady_clock::now();

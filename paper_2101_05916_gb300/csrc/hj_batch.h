@@ -3,6 +3,7 @@
 
 #include <chrono>
 #include <map>
+#include <string>
 #include <vector>
 
 #include "hj_grid.h"
@@ -100,7 +101,7 @@ class Runner {
   std::vector<Group> groups_;
   bool dirty_ = true;
   std::vector<int> order_;  // slots in the current item list
-  std::map<long long, cudaGraphExec_t> graphs_;  // round length -> graph
+  std::map<std::string, cudaGraphExec_t> graphs_;  // round shape -> graph
   cudaStream_t cap_stream_ = nullptr;
 };
 

@@ -123,6 +123,9 @@ struct hj_server_s {
   std::deque<long long> queue;
   std::map<long long, long long> resident_of_key;  // key -> ticket holding the prior
   size_t used = 0;
+  int order = HJ_ORDER_FIFO;
+  long long max_active_nodes = 0;
+  long long active_nodes = 0;
   hj_server_stats st{};
   std::vector<double> latencies;
   bool first_submit_seen = false;
@@ -163,7 +166,19 @@ bool hj_server_s::evict_locked(size_t need) {
   return true;
 }
 
+// Estimated work of a request: nodes x largest axis length (steps ~ 1 / h).
+static double est_work(const Req& q) {
+  int m = 1;
+  for (int i = 0; i < q.r.ndim; ++i) m = std::max(m, q.r.n[i]);
+  return (double)q.npts * (double)m;
+}
+
 void hj_server_s::admit_locked(std::vector<long long>& admitted) {
+  if (order == HJ_ORDER_SHORTEST && queue.size() > 1) {
+    std::stable_sort(queue.begin(), queue.end(), [&](long long a, long long b) {
+      return est_work(reqs[a]) < est_work(reqs[b]);
+    });
+  }
   for (auto it = queue.begin(); it != queue.end();) {
     if (runner->active() >= max_active) break;
     Req& q = reqs[*it];
@@ -174,6 +189,13 @@ void hj_server_s::admit_locked(std::vector<long long>& admitted) {
       st.failed++;
       it = queue.erase(it);
       cv_done.notify_all();
+      continue;
+    }
+    // the node cap keeps large grids from time-slicing each other; grids
+    // below 1/64 of it ride along regardless (they barely load the GPU)
+    if (max_active_nodes > 0 && runner->active() > 0 && q.npts * 64 > max_active_nodes &&
+        active_nodes + q.npts > max_active_nodes) {
+      ++it;
       continue;
     }
     if (used + q.bytes > budget && !evict_locked(q.bytes)) {
@@ -215,6 +237,7 @@ void hj_server_s::admit_locked(std::vector<long long>& admitted) {
     q.slot = slot;
     q.state = Q_RUNNING;
     used += q.bytes;
+    active_nodes += q.npts;
     st.peak_bytes = std::max<long long>(st.peak_bytes, (long long)used);
     st.admitted++;
     if (mode == HJ_WARM) st.warm_starts++; else st.cold_starts++;
@@ -259,6 +282,7 @@ void hj_server_s::run() {
         q.t_done = now;
         q.last_use = now;
         t_last_done = now;
+        active_nodes -= q.npts;
         latencies.push_back(s.wall_ms);
         // grid-point updates count for every request that stepped, converged or not
         st.updates += (double)q.npts * (double)s.steps;
@@ -448,6 +472,17 @@ hj_status hj_server_cancel(hj_server s, long long ticket) {
   auto it = s->reqs.find(ticket);
   if (it == s->reqs.end()) return hja::fail(HJ_ERR_ARG, "unknown ticket %lld", ticket);
   it->second.cancel = true;
+  s->cv_work.notify_all();
+  return HJ_OK;
+}
+
+hj_status hj_server_set_policy(hj_server s, int order, long long max_active_nodes) {
+  if (!s) return hja::fail(HJ_ERR_ARG, "NULL server");
+  if (order != HJ_ORDER_FIFO && order != HJ_ORDER_SHORTEST) return hja::fail(HJ_ERR_ARG, "bad order");
+  if (max_active_nodes < 0) return hja::fail(HJ_ERR_ARG, "max_active_nodes must be >= 0");
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->order = order;
+  s->max_active_nodes = max_active_nodes;
   s->cv_work.notify_all();
   return HJ_OK;
 }

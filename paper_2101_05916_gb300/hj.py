@@ -26,6 +26,7 @@ HJ_DRIFT, HJ_QUAD_Z, HJ_QUAD_X4 = 0, 1, 2
 HJ_FIRST, HJ_ENO2, HJ_WENO5 = 1, 2, 5
 HJ_CLAMP_VI, HJ_CLAMP_MONOTONE = 0, 1
 HJ_COLD, HJ_WARM = 0, 1
+HJ_ORDER_FIFO, HJ_ORDER_SHORTEST = 0, 1
 HJ_MAX_DIM = 4
 
 STATUS_NAMES = {0: "HJ_OK", 1: "HJ_ERR_ARG", 2: "HJ_ERR_OOM", 3: "HJ_ERR_CUDA",
@@ -111,6 +112,7 @@ SIGNATURES = {
     "hj_server_release": (_i, [_vp, _ll]),
     "hj_server_cancel": (_i, [_vp, _ll]),
     "hj_server_get_stats": (_i, [_vp, _P(hj_server_stats)]),
+    "hj_server_set_policy": (_i, [_vp, _i, _ll]),
     "hj_solve_fixed_static": (_i, [_i, _P(_i), _P(_d), _P(_d), _i, _P(_d), _i, _P(_d), _P(_d),
                                    _i, _P(_d), _P(_d), _i, _i, _d, _ll, _i, _vp, _vp]),
 }
@@ -398,6 +400,10 @@ def hj_server_release(s: int, ticket: int) -> None:
 
 def hj_server_cancel(s: int, ticket: int) -> None:
     _check(lib().hj_server_cancel(s, ticket))
+
+
+def hj_server_set_policy(s: int, order: int = HJ_ORDER_FIFO, max_active_nodes: int = 0) -> None:
+    _check(lib().hj_server_set_policy(s, int(order), int(max_active_nodes)))
 
 
 def hj_server_get_stats(s: int) -> Dict:

@@ -47,9 +47,14 @@ def solve_opts_for(req) -> Dict:
 
 
 def replay_server(trace: Sequence, budget_bytes: int = 40 << 30, max_active: int = 64,
-                  time_scale: float = 1.0, warm: bool = True, stream=None) -> Dict:
-    """Replay `trace` (workloads.Request list); returns latency stats."""
+                  time_scale: float = 1.0, warm: bool = True, stream=None,
+                  order: int = hj.HJ_ORDER_SHORTEST, max_active_nodes: int = 6_000_000) -> Dict:
+    """Replay `trace` (workloads.Request list); returns latency stats.
+
+    Default policy: shortest estimated work first, at most 6M nodes of large
+    grids stepping at once (small grids ride along)."""
     s = hj.hj_server_create(budget_bytes, max_active, stream)
+    hj.hj_server_set_policy(s, order, max_active_nodes)
     tickets: List[int] = [0] * len(trace)
     t0 = time.perf_counter()
 

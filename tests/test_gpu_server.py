@@ -181,3 +181,29 @@ def test_trace_replay_small(hj):
     assert all(rc == 0 for rc in res["statuses"])
     assert res["server"]["completed"] == 12
     assert res["p99_ms"] >= res["p50_ms"] > 0.0
+
+
+def test_shortest_first_policy_with_node_cap(hj):
+    """With shortest-first admission and a node cap, small requests submitted
+    after a large one run beside it and finish first; every result is the
+    same as its single-grid solve."""
+    s = hj.hj_server_create(8 << 30, 16)
+    hj.hj_server_set_policy(s, hj.HJ_ORDER_SHORTEST, 30 ** 4)
+    big = wl.quad_x4(31, 0.5)
+    small = [wl.quad_z(41 + 4 * i, 0.5) for i in range(6)]
+    tb = run(hj, s, big, 5, 0.5, clamp=1, fixed_steps=4000)
+    ts = [run(hj, s, sp, 2, 0.0) for sp in small]
+    outs = [fetch(hj, s, t, sp) for t, sp in zip(ts, small)]
+    rb, stb, _ = fetch(hj, s, tb, big)
+    hj.hj_server_destroy(s)
+    assert rb == hj.HJ_OK and all(o[0] == hj.HJ_OK for o in outs)
+    assert max(o[1]["wall_ms"] for o in outs) < stb["wall_ms"]
+    for (rc, st, W), sp in zip(outs, small):
+        g = hj.Grid.from_spec(sp)
+        g.solve(hj.HJ_COLD, scheme=2, max_steps=20000)
+        assert np.array_equal(W, g.value())
+        g.close()
+    s2 = hj.hj_server_create(1 << 20, 1)
+    with pytest.raises(hj.HJError):
+        hj.hj_server_set_policy(s2, 7, 0)
+    hj.hj_server_destroy(s2)
