@@ -15,7 +15,11 @@ resident across steps).
 
 Other lines: `e2e` repeats the step through the same C ABI with the prior
 uploaded from pinned host memory and both results read back.
-`latency_ms` gives p50/p99 of the cold solve and the warm update.
+`latency_ms` gives p50/p99 of the cold solve and the warm update, and of the
+served form vs one-at-a-time cold solves on the first requests of the seeded
+serving trace.  `scenarios` holds the decomposed batched update (x, y at 61^4
+and z at 201^2, wind 0 -> 0.5 -> 1.0 -> 1.5), the coarse-to-fine solve
+(31^4 -> 81^4), and the serving sample.
 `roofline` times the dominant stage kernel in a separate fixed-step pass with
 CUDA events.  `cpu_baseline` is the FP64 oracle timed on a bounded sample of
 the same workload.
@@ -42,6 +46,7 @@ UNIT = "grid-point updates/s"
 N_AXIS = 41
 BOUND_PRIOR, BOUND = 0.0, 0.5
 BAND = 0.5
+MARGIN = 0
 CLAMP = 1  # HJ_CLAMP_MONOTONE
 
 # Algorithmic work per grid-point update (one node, one full TVD-RK3 step),
@@ -70,6 +75,9 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-scenarios", action="store_true",
+                    help="skip the decomposed / adaptive-grid / serving scenarios")
+    ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="run only this many fixed TVD-RK3 steps of the workload (for ncu)")
     return ap.parse_args()
@@ -269,14 +277,15 @@ def main():
         g.close()
         return
     st_prior = g.solve(hj.HJ_COLD, scheme=5, max_steps=200000, max_wall_ms=120000.0, band=BAND,
-                       clamp=CLAMP)
+                       band_margin=MARGIN, clamp=CLAMP)
     assert st_prior["converged"], st_prior
     prior = torch.empty(npts, dtype=torch.float32, device="cuda")
     g.value_into(prior)
     g.set_disturbance_bound([-BOUND], [BOUND])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
-    cap = dict(scheme=5, max_steps=200000, max_wall_ms=120000.0, band=BAND, clamp=CLAMP)
+    cap = dict(scheme=5, max_steps=200000, max_wall_ms=120000.0, band=BAND, band_margin=MARGIN,
+               clamp=CLAMP)
 
     def step():
         c = g.solve(hj.HJ_COLD, **cap)
@@ -376,8 +385,30 @@ def main():
                "h2d_bytes_per_step": 4 * npts, "d2h_bytes_per_step": 8 * npts}
 
     g.close()
+
+    # ---- scenarios: the paper's accelerations against the plain cold way
+    scen = None
+    if not args.no_scenarios:
+        from paper_2101_05916_gb300 import scenarios
+        ref = scenarios.load_reference(os.path.join(ROOT, "tests", "golden",
+                                                    "x41_b1.0_monotone_band_samples.txt"))
+        scen = {"decomposed_update": scenarios.decomposed_update(),
+                "adaptive_grid": scenarios.adaptive_grid(reference=ref),
+                "serving": scenarios.serving(args.serve_requests)}
     if rank != 0:
         return
+    latency = {
+        "x41_cold_p50": float(np.percentile(cold_ms, 50)),
+        "x41_cold_p99": float(np.percentile(cold_ms, 99)),
+        "x41_warm_update_p50": float(np.percentile(warm_ms, 50)),
+        "x41_warm_update_p99": float(np.percentile(warm_ms, 99)),
+        "x41_cold_steps": int(np.median(cold_steps)), "x41_warm_steps": int(np.median(warm_steps))}
+    if scen is not None:
+        sv = scen["serving"]
+        latency.update({"served_p50": sv["served"]["p50_ms"], "served_p99": sv["served"]["p99_ms"],
+                        "plain_cold_p50": sv["plain_cold"]["p50_ms"],
+                        "plain_cold_p99": sv["plain_cold"]["p99_ms"],
+                        "serving_requests": sv["requests"]})
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
@@ -387,16 +418,14 @@ def main():
                    "scheme": "WENO5", "rk": "TVD-RK3", "cfl": 0.5, "tol": 1e-4,
                    "check_dt": 0.1, "stop_band": BAND, "clamp": "monotone", "wind_prior": BOUND_PRIOR, "wind": BOUND,
                    "l2": "flushed between timed steps", "parallelism": "independent grids per rank"},
-        "latency_ms": {
-            "cold_p50": float(np.percentile(cold_ms, 50)), "cold_p99": float(np.percentile(cold_ms, 99)),
-            "warm_update_p50": float(np.percentile(warm_ms, 50)),
-            "warm_update_p99": float(np.percentile(warm_ms, 99)),
-            "cold_steps": int(np.median(cold_steps)), "warm_steps": int(np.median(warm_steps))},
+        "latency_ms": latency,
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    if scen is not None:
+        line["scenarios"] = scen
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line))

@@ -30,7 +30,8 @@
  *     over the grid and the input boxes.
  *   - Integration: TVD-RK3, then the clamp after each full step.
  *   - Stop: when max|W(t + check_dt) - W(t)| < tol, over every node or over
- *     the band |W| <= opts.band around the zero level set.
+ *     the band |W| <= opts.band around the zero level set, optionally
+ *     skipping opts.band_margin cells next to the faces of the grid box.
  *
  * Threading and memory:
  *   - Handles are not thread-safe.  Use one handle per thread, or serialise
@@ -101,6 +102,11 @@ typedef struct {
                          /* min(|W|, |W_window_start|) <= band, i.e. the band around the  */
                          /* zero level set that bounds the safe set (Sec. II-A).          */
                          /* 0 (default): every node.                                      */
+  int autotune;          /* 1: pick the stage-kernel block size by timing (hj_autotune)   */
+                         /* once per grid shape before solving (default 0)                */
+  int band_margin;       /* the stop test skips nodes closer than this many cells to a    */
+                         /* face of an unconstrained axis (every axis for a ball), where  */
+                         /* trajectories leave a truncated grid (default 0)               */
 } hj_solve_opts;
 
 typedef struct {
@@ -345,6 +351,15 @@ hj_status hj_solve_fixed_static(int ndim, const int* n, const double* lo, const 
                                 const double* box_lo, const double* box_hi, int mode,
                                 int scheme, double dt, long long steps, int clamp, float* W,
                                 void* cuda_stream);
+
+/* Launch-shape autotuner.  It picks the stage kernel's threads per block
+ * (128, 256 or 512) for this grid and scheme.  It times a few TVD-RK3 steps
+ * of each candidate on the grid's current value, or on l if the grid holds
+ * none, and keeps the fastest.  W is left unchanged.  The choice is cached
+ * per (model, ndim, scheme, grid shape) for the whole process, and later
+ * solves of this grid use it.  *threads_out (may be NULL) receives the
+ * choice. */
+hj_status hj_autotune(hj_grid g, int scheme, int* threads_out);
 
 /* Number of nodes of the grid. */
 long long hj_grid_points(hj_grid g);

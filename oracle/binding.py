@@ -37,7 +37,8 @@ class _Opts(ctypes.Structure):
     _fields_ = [("scheme", ctypes.c_int), ("cfl", ctypes.c_double), ("dt", ctypes.c_double),
                 ("tol", ctypes.c_double), ("check_dt", ctypes.c_double),
                 ("max_steps", ctypes.c_long), ("fixed_steps", ctypes.c_long),
-                ("clamp", ctypes.c_int), ("warm", ctypes.c_int), ("band", ctypes.c_double)]
+                ("clamp", ctypes.c_int), ("warm", ctypes.c_int), ("band", ctypes.c_double),
+                ("band_margin", ctypes.c_int)]
 
 
 class _Stats(ctypes.Structure):
@@ -125,14 +126,14 @@ def set_num_threads(k: int) -> None:
 def solve(spec, scheme: int = 5, cfl: float = 0.5, dt: float = 0.0, tol: float = 1e-4,
           check_dt: float = 0.1, max_steps: int = 0, fixed_steps: int = 0,
           clamp: int = 0, warm: Optional[np.ndarray] = None,
-          band: float = 0.0) -> Tuple[np.ndarray, Dict]:
+          band: float = 0.0, band_margin: int = 0) -> Tuple[np.ndarray, Dict]:
     """Run the oracle solve; returns (W on the grid, stats)."""
     W = np.zeros(spec.n, dtype=np.float64)
     if warm is not None:
         W[...] = warm
     o = _Opts(scheme=scheme, cfl=cfl, dt=dt, tol=tol, check_dt=check_dt, max_steps=max_steps,
               fixed_steps=fixed_steps, clamp=clamp, warm=1 if warm is not None else 0,
-              band=band)
+              band=band, band_margin=band_margin)
     st = _Stats()
     pr = _problem(spec)
     rc = lib().or_solve(ctypes.byref(pr), ctypes.byref(o), _dp(W), ctypes.byref(st))

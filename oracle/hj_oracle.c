@@ -22,8 +22,10 @@
  * below a tolerance (Sec. II-A: iterate "until convergence"; the converged
  * value is the infinite-horizon fixed point).  Optionally the stop test only
  * watches a band |W| <= band around the zero level set that bounds the safe
- * set S (Sec. II-A); far inside S, high-order schemes on a truncated grid can
- * keep cycling without moving S.
+ * set S (Sec. II-A), and only nodes at least band_margin cells inside the
+ * grid box.  High-order schemes on a truncated grid can keep cycling far
+ * inside S and next to the faces where trajectories leave the grid, without
+ * moving S.
  *
  * The paper names no numerical scheme.  The discrete operator below is the
  * textbook one (Osher & Fedkiw 2003, Sec. 3.3-3.4 and 5.3; Jiang & Peng 2000;
@@ -95,6 +97,9 @@ typedef struct {
   int warm;          /* 0 = start from l, 1 = start from min(W_in, l)     */
   double band;       /* > 0: the stop test only watches nodes with
                         min(|W|, |W_window_start|) <= band                 */
+  int band_margin;   /* the stop test skips nodes closer than this many
+                        cells to a face of an axis the box constraint
+                        leaves free (every axis for a ball)                 */
 } or_opts;
 
 typedef struct {
@@ -445,6 +450,19 @@ int or_solve(const or_problem* P, const or_opts* o, double* W, or_stats* st) {
       double r = 0.0;
       for (long i = 0; i < npts; ++i) {
         if (o->band > 0.0 && fmin(fabs(W[i]), fabs(snap[i])) > o->band) continue;
+        if (o->band_margin > 0) {
+          /* faces of axes the box constraint leaves free */
+          long idx[OR_MAXD];
+          grid_unravel(P, i, idx);
+          int inside = 1;
+          for (int d = 0; d < P->ndim; ++d) {
+            int constrained = P->con_kind == OR_CON_BOX &&
+                              !(isinf(P->con_a[d]) && isinf(P->con_b[d]));
+            if (constrained) continue;
+            if (idx[d] < o->band_margin || idx[d] > P->n[d] - 1 - o->band_margin) inside = 0;
+          }
+          if (!inside) continue;
+        }
         double e = fabs(W[i] - snap[i]);
         if (e > r) r = e;
       }

@@ -15,7 +15,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <string>
 
 #include "hj_grid.h"
 
@@ -138,40 +141,43 @@ static void invalidate(hj_grid g) {
 
 // k TVD-RK3 steps; the last one folds the window residual when check_last.
 static cudaError_t enqueue_steps(hj_grid g, const hjd::DevGrid& d, int scheme, int clamp,
-                                 float band, float dt, long long k, bool check_last,
+                                 float band, int margin, float dt, long long k, bool check_last,
                                  cudaStream_t s) {
-  hjd::StageArgs a1{g->W, g->W, g->A, nullptr, nullptr, dt, 0, clamp, band};
-  hjd::StageArgs a2{g->A, g->W, g->B, nullptr, nullptr, dt, 0, clamp, band};
-  hjd::StageArgs a3{g->B, g->W, g->W, g->snap, g->dscal + 4, dt, 0, clamp, band};
+  hjd::StageArgs a1{g->W, g->W, g->A, nullptr, nullptr, dt, 0, clamp, band, margin};
+  hjd::StageArgs a2{g->A, g->W, g->B, nullptr, nullptr, dt, 0, clamp, band, margin};
+  hjd::StageArgs a3{g->B, g->W, g->W, g->snap, g->dscal + 4, dt, 0, clamp, band, margin};
+  const int t = g->threads;
   for (long long i = 0; i < k; ++i) {
     cudaError_t e;
-    if ((e = hjk::launch_stage(d, scheme, 1, a1, s)) != cudaSuccess) return e;
-    if ((e = hjk::launch_stage(d, scheme, 2, a2, s)) != cudaSuccess) return e;
+    if ((e = hjk::launch_stage(d, scheme, 1, a1, s, t)) != cudaSuccess) return e;
+    if ((e = hjk::launch_stage(d, scheme, 2, a2, s, t)) != cudaSuccess) return e;
     a3.check = (check_last && i == k - 1) ? 1 : 0;
-    if ((e = hjk::launch_stage(d, scheme, 3, a3, s)) != cudaSuccess) return e;
+    if ((e = hjk::launch_stage(d, scheme, 3, a3, s, t)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
 // One check window: reset the residual, k steps, copy the residual to pinned host memory.
 static cudaError_t enqueue_window(hj_grid g, const hjd::DevGrid& d, int scheme, int clamp,
-                                  float band, float dt, long long k, cudaStream_t s) {
+                                  float band, int margin, float dt, long long k, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(g->dscal + 4, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
-  if ((e = enqueue_steps(g, d, scheme, clamp, band, dt, k, true, s)) != cudaSuccess) return e;
+  if ((e = enqueue_steps(g, d, scheme, clamp, band, margin, dt, k, true, s)) != cudaSuccess)
+    return e;
   return cudaMemcpyAsync(g->hscal + 4, g->dscal + 4, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
 }
 
 static hj_status run_window(hj_grid g, const hjd::DevGrid& d, int scheme, int clamp, float band,
-                            float dt, long long k, bool use_graph) {
+                            int margin, float dt, long long k, bool use_graph) {
   if (use_graph && k <= 4096) {
     if (!(g->gexec && g->g_per == k && g->g_dt == dt && g->g_scheme == scheme &&
-          g->g_clamp == clamp && g->g_band == band)) {
+          g->g_clamp == clamp && g->g_band == band && g->g_margin == margin &&
+          g->g_threads == g->threads)) {
       drop_graph(g);
       cudaGraph_t graph = nullptr;
       HJ_CU(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
       unsigned long long before = hjk::g_launches.load();
-      cudaError_t e = enqueue_window(g, d, scheme, clamp, band, dt, k, g->cap_stream);
+      cudaError_t e = enqueue_window(g, d, scheme, clamp, band, margin, dt, k, g->cap_stream);
       cudaError_t e2 = cudaStreamEndCapture(g->cap_stream, &graph);
       // launches recorded during capture run later, on replay
       hjk::g_launches.store(before);
@@ -191,13 +197,89 @@ static hj_status run_window(hj_grid g, const hjd::DevGrid& d, int scheme, int cl
       g->g_scheme = scheme;
       g->g_clamp = clamp;
       g->g_band = band;
+      g->g_margin = margin;
+      g->g_threads = g->threads;
     }
     HJ_CU(cudaGraphLaunch(g->gexec, g->stream));
     hjk::g_launches.fetch_add(3ull * (unsigned long long)k);
   } else {
-    HJ_CU(enqueue_window(g, d, scheme, clamp, band, dt, k, g->stream));
+    HJ_CU(enqueue_window(g, d, scheme, clamp, band, margin, dt, k, g->stream));
   }
   HJ_CU(cudaStreamSynchronize(g->stream));
+  return HJ_OK;
+}
+
+// Block sizes tried by the autotuner, and the process-wide choices per
+// (model, ndim, scheme, grid shape).
+static const int kCandidates[3] = {128, 256, 512};
+static std::mutex g_tune_mu;
+static std::map<std::string, int> g_tuned;
+
+static std::string tune_key(const hj_grid g, int scheme) {
+  std::string k = std::to_string(g->model) + "/" + std::to_string(scheme);
+  for (int i = 0; i < g->ndim; ++i) k += "/" + std::to_string(g->n[i]);
+  return k;
+}
+
+// Pick the stage-kernel block size for this grid: time a few TVD-RK3 steps
+// of each candidate on the grid's own current field, keep the fastest.  W is
+// saved to the snapshot field first and restored afterwards, so the grid's
+// value is unchanged.  Choices are cached per grid shape for the process.
+hj_status autotune(hj_grid g, int scheme, int clamp) {
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(tune_key(g, scheme));
+    if (it != g_tuned.end()) {
+      g->threads = it->second;
+      g->tuned_scheme = scheme;
+      return HJ_OK;
+    }
+  }
+  hj_status st = ensure_alpha(g);
+  if (st != HJ_OK) return st;
+  double dt = cfl_dt(g, 0.5);
+  if (!(dt > 0.0)) dt = 1e-3;
+  hjd::DevGrid d = devgrid(g);
+  if (!g->has_value) HJ_CU(hjk::launch_init(d, g->W, g->snap, 0, g->stream));
+  size_t bytes = (size_t)g->npts * sizeof(float);
+  HJ_CU(cudaMemcpyAsync(g->snap, g->W, bytes, cudaMemcpyDeviceToDevice, g->stream));
+  long long steps = std::max(2ll, std::min(20ll, 400000000ll / std::max(1ll, g->npts)));
+  cudaEvent_t e0, e1;
+  HJ_CU(cudaEventCreate(&e0));
+  HJ_CU(cudaEventCreate(&e1));
+  int best = g->threads;
+  float best_ms = 1e30f;
+  int saved = g->threads;
+  for (int c : kCandidates) {
+    g->threads = c;
+    cudaError_t e = enqueue_steps(g, d, scheme, clamp, 0.f, 0, (float)dt, 1, false, g->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, g->stream);
+    if (e == cudaSuccess)
+      e = enqueue_steps(g, d, scheme, clamp, 0.f, 0, (float)dt, steps, false, g->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, g->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      g->threads = saved;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return fail(HJ_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
+    }
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+    HJ_CU(cudaMemcpyAsync(g->W, g->snap, bytes, cudaMemcpyDeviceToDevice, g->stream));
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  HJ_CU(cudaStreamSynchronize(g->stream));
+  g->threads = best;
+  g->tuned_scheme = scheme;
+  drop_graph(g);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned[tune_key(g, scheme)] = best;
   return HJ_OK;
 }
 
@@ -232,6 +314,8 @@ void hj_default_opts(hj_solve_opts* o) {
   o->clamp = HJ_CLAMP_VI;
   o->use_graph = 1;
   o->band = 0.0;
+  o->autotune = 0;
+  o->band_margin = 0;
 }
 
 void hj_grid_destroy(hj_grid g) {
@@ -401,6 +485,16 @@ hj_status hj_set_disturbance_bound(hj_grid g, const double* d_lo, const double* 
   return HJ_OK;
 }
 
+hj_status hj_autotune(hj_grid g, int scheme, int* threads_out) {
+  if (!g) return fail(HJ_ERR_ARG, "grid is NULL");
+  hj_status st = validate_ready(g, scheme);
+  if (st != HJ_OK) return st;
+  DeviceGuard dg(g->device);
+  if ((st = autotune(g, scheme, HJ_CLAMP_VI)) != HJ_OK) return st;
+  if (threads_out) *threads_out = g->threads;
+  return HJ_OK;
+}
+
 hj_status hj_alpha(hj_grid g, double* alpha_out) {
   if (!g || !alpha_out) return fail(HJ_ERR_ARG, "NULL argument");
   if (g->model < 0) return fail(HJ_ERR_STATE, "dynamics not set");
@@ -419,7 +513,8 @@ hj_status hj_solve(hj_grid g, int mode, const hj_solve_opts* o_in, hj_solve_stat
   hj_default_opts(&o);
   if (o_in) o = *o_in;
   if (mode != HJ_COLD && mode != HJ_WARM) return fail(HJ_ERR_ARG, "mode must be HJ_COLD or HJ_WARM");
-  if (!(o.cfl > 0.0) || !(o.tol >= 0.0) || !(o.check_dt > 0.0) || o.dt < 0.0 || !(o.band >= 0.0))
+  if (!(o.cfl > 0.0) || !(o.tol >= 0.0) || !(o.check_dt > 0.0) || o.dt < 0.0 || !(o.band >= 0.0) ||
+      o.band_margin < 0)
     return fail(HJ_ERR_ARG, "bad solve options");
   if (o.clamp != HJ_CLAMP_VI && o.clamp != HJ_CLAMP_MONOTONE) return fail(HJ_ERR_ARG, "bad clamp");
   hj_status st = validate_ready(g, o.scheme);
@@ -431,6 +526,8 @@ hj_status hj_solve(hj_grid g, int mode, const hj_solve_opts* o_in, hj_solve_stat
   std::memset(&stats, 0, sizeof(stats));
 
   if ((st = ensure_alpha(g)) != HJ_OK) return st;
+  if (o.autotune && g->tuned_scheme != o.scheme && (st = autotune(g, o.scheme, o.clamp)) != HJ_OK)
+    return st;
   double dt = o.dt > 0.0 ? o.dt : cfl_dt(g, o.cfl);
   stats.dt = dt;
   hjd::DevGrid d = devgrid(g);
@@ -443,8 +540,8 @@ hj_status hj_solve(hj_grid g, int mode, const hj_solve_opts* o_in, hj_solve_stat
     HJ_CU(cudaStreamSynchronize(g->stream));
     stats.converged = 1;
   } else if (o.fixed_steps > 0) {
-    HJ_CU(enqueue_steps(g, d, o.scheme, o.clamp, (float)o.band, fdt, o.fixed_steps, false,
-                        g->stream));
+    HJ_CU(enqueue_steps(g, d, o.scheme, o.clamp, (float)o.band, o.band_margin, fdt, o.fixed_steps,
+                        false, g->stream));
     HJ_CU(cudaStreamSynchronize(g->stream));
     stats.steps = o.fixed_steps;
   } else {
@@ -453,7 +550,7 @@ hj_status hj_solve(hj_grid g, int mode, const hj_solve_opts* o_in, hj_solve_stat
     for (;;) {
       long long todo = per;
       if (o.max_steps > 0 && stats.steps + todo > o.max_steps) todo = o.max_steps - stats.steps;
-      st = run_window(g, d, o.scheme, o.clamp, (float)o.band, fdt, todo,
+      st = run_window(g, d, o.scheme, o.clamp, (float)o.band, o.band_margin, fdt, todo,
                       o.use_graph != 0 && todo == per);
       if (st != HJ_OK) return st;
       stats.steps += todo;

@@ -162,7 +162,8 @@ hj_status Runner::add(hj_grid g, int mode, const hj_solve_opts& o, int* slot_out
   if (!g) return hja::fail(HJ_ERR_ARG, "grid is NULL");
   if (g->device != device_) return hja::fail(HJ_ERR_ARG, "batch grids must share one device");
   if (mode != HJ_COLD && mode != HJ_WARM) return hja::fail(HJ_ERR_ARG, "bad mode");
-  if (!(o.cfl > 0.0) || !(o.tol >= 0.0) || !(o.check_dt > 0.0) || o.dt < 0.0 || !(o.band >= 0.0))
+  if (!(o.cfl > 0.0) || !(o.tol >= 0.0) || !(o.check_dt > 0.0) || o.dt < 0.0 || !(o.band >= 0.0) ||
+      o.band_margin < 0)
     return hja::fail(HJ_ERR_ARG, "bad solve options");
   hj_status st = hja::validate_ready(g, o.scheme);
   if (st != HJ_OK) return st;
@@ -182,6 +183,8 @@ hj_status Runner::add(hj_grid g, int mode, const hj_solve_opts& o, int* slot_out
   if (k < 0) return hja::fail(HJ_ERR_OOM, "batch is full (%d grids)", cap_);
   hja::DeviceGuard dg(device_);
   if ((st = hja::ensure_alpha(g)) != HJ_OK) return st;
+  if (o.autotune && g->tuned_scheme != o.scheme && (st = hja::autotune(g, o.scheme, o.clamp)) != HJ_OK)
+    return st;
   double dt = o.dt > 0.0 ? o.dt : hja::cfl_dt(g, o.cfl);
   // order the grid's own stream before the batch stream
   if (g->stream != stream_) HJ_CU(cudaStreamSynchronize(g->stream));
@@ -195,6 +198,7 @@ hj_status Runner::add(hj_grid g, int mode, const hj_solve_opts& o, int* slot_out
   s.scheme = o.scheme;
   s.clamp = o.clamp;
   s.band = (float)o.band;
+  s.margin = o.band_margin;
   s.dt = dt;
   s.max_wall_ms = o.max_wall_ms;
   s.t0 = std::chrono::steady_clock::now();
@@ -271,9 +275,9 @@ hj_status Runner::rebuild() {
     Item& it = gr.pack.items[gr.pack.count];
     it.g = hja::devgrid(g);
     float dt = (float)s.dt;
-    it.a[0] = hjd::StageArgs{g->W, g->W, g->A, nullptr, nullptr, dt, 0, s.clamp, s.band};
-    it.a[1] = hjd::StageArgs{g->A, g->W, g->B, nullptr, nullptr, dt, 0, s.clamp, s.band};
-    it.a[2] = hjd::StageArgs{g->B, g->W, g->W, g->snap, nullptr, dt, 1, s.clamp, s.band};
+    it.a[0] = hjd::StageArgs{g->W, g->W, g->A, nullptr, nullptr, dt, 0, s.clamp, s.band, s.margin};
+    it.a[1] = hjd::StageArgs{g->A, g->W, g->B, nullptr, nullptr, dt, 0, s.clamp, s.band, s.margin};
+    it.a[2] = hjd::StageArgs{g->B, g->W, g->W, g->snap, nullptr, dt, 1, s.clamp, s.band, s.margin};
     it.kind = by_kind[j].first;
     it.slot = k;
     it.bx = (it.g.plane + kThreads - 1) / kThreads;
@@ -318,7 +322,8 @@ cudaError_t Runner::enqueue_round(long long R, cudaStream_t s) {
           long long s1 = c.steps + i + 1;
           a.check = (stage == 3 && (s1 % c.per == 0 || s1 >= c.max_steps)) ? 1 : 0;
           a.resid = &dev_ctl_[it.slot].resid;
-          cudaError_t e = hjk::launch_stage(it.g, it.kind % 10, stage, a, s);
+          cudaError_t e = hjk::launch_stage(it.g, it.kind % 10, stage, a, s,
+                                            slots_[it.slot].g->threads);
           if (e != cudaSuccess) return e;
         } else if (!launch_kind(gr.kind, gr.pack, gr.blocks, dev_ctl_, s, stage)) {
           return cudaErrorInvalidValue;

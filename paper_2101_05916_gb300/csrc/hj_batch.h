@@ -75,6 +75,7 @@ class Runner {
     bool used = false, done = false, fixed = false, wall_capped = false;
     int scheme = 5, clamp = 0;
     float band = 0.f;
+    int margin = 0;
     double dt = 0.0, max_wall_ms = 0.0;
     std::chrono::steady_clock::time_point t0;
     double wall_ms = 0.0;

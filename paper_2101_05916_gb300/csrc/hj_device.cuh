@@ -65,6 +65,7 @@ struct StageArgs {
   int check;
   int clamp;           // 0: min(W3, l); 1: min(W3, l, W)
   float band;          // > 0: residual only where min(|W|, |snap|) <= band
+  int margin;          // residual only at nodes >= margin cells from every face
 };
 
 __device__ __forceinline__ float rcp_approx(float x) {

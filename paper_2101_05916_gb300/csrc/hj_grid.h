@@ -37,6 +37,8 @@ struct hj_grid_s {
 
   bool has_value = false;
   bool alpha_valid = false;
+  int threads = 256;        // stage-kernel block size (hj_autotune may change it)
+  int tuned_scheme = 0;     // scheme the block size was tuned for (0 = not tuned)
   float alpha[HJ_MAX_DIM] = {0, 0, 0, 0};
 
   cudaGraphExec_t gexec = nullptr;  // cached graph of one check window
@@ -44,6 +46,8 @@ struct hj_grid_s {
   float g_dt = 0.f;
   int g_scheme = 0, g_clamp = 0;
   float g_band = 0.f;
+  int g_margin = 0;
+  int g_threads = 0;
 };
 
 namespace hja {
@@ -52,6 +56,7 @@ hj_status fail(hj_status s, const char* fmt, ...);
 hjd::DevGrid devgrid(const hj_grid g);
 hj_status ensure_alpha(hj_grid g);
 hj_status validate_ready(hj_grid g, int scheme);
+hj_status autotune(hj_grid g, int scheme, int clamp);
 double cfl_dt(const hj_grid g, double cfl);
 
 struct DeviceGuard {

@@ -15,9 +15,10 @@ extern std::atomic<unsigned long long> g_launches;
 // Threads per block of the stencil kernels.
 constexpr int kStageThreads = 256;
 
-// One TVD-RK3 stage on one grid.  stage is 1, 2 or 3; scheme 1, 2 or 5.
+// One TVD-RK3 stage on one grid.  stage is 1, 2 or 3; scheme 1, 2 or 5;
+// threads per block 128, 256 or 512 (other values use 256).
 cudaError_t launch_stage(const hjd::DevGrid& g, int scheme, int stage, const hjd::StageArgs& a,
-                         cudaStream_t s);
+                         cudaStream_t s, int threads = kStageThreads);
 // Per-axis max |f_i| over grid nodes and input vertices, as float bits into out[0..ndim).
 // out must be zeroed first.
 cudaError_t launch_alpha(const hjd::DevGrid& g, unsigned* out, cudaStream_t s);

@@ -30,8 +30,8 @@ std::atomic<unsigned long long> g_launches{0};
 using hjd::DevGrid;
 using hjd::StageArgs;
 
-template <int D, int S, int M, int STAGE>
-__global__ void __launch_bounds__(kStageThreads) stage_kernel(const DevGrid g, const StageArgs a) {
+template <int D, int S, int M, int STAGE, int THREADS>
+__global__ void __launch_bounds__(THREADS) stage_kernel(const DevGrid g, const StageArgs a) {
   unsigned r = hjd::stage_point<D, S, M, STAGE>(g, a, blockIdx.x * blockDim.x + threadIdx.x,
                                                 blockIdx.y, a.check != 0);
   if constexpr (STAGE == 3) {
@@ -190,19 +190,29 @@ __global__ void query_kernel(const DevGrid g, const float* __restrict__ W, int n
 
 // ------------------------------------------------------------- dispatch
 
-static dim3 stage_grid(const DevGrid& g) {
-  unsigned bx = (unsigned)((g.plane + kStageThreads - 1) / kStageThreads);
+static dim3 stage_grid(const DevGrid& g, int threads) {
+  unsigned bx = (unsigned)((g.plane + threads - 1) / threads);
   unsigned by = g.ndim == 4 ? (unsigned)g.n[0] : 1u;
   return dim3(bx, by, 1u);
 }
 
-template <int D, int S, int M>
-static cudaError_t stage_dispatch(const DevGrid& g, int stage, const StageArgs& a, cudaStream_t s) {
-  dim3 grid = stage_grid(g), block(kStageThreads);
+template <int D, int S, int M, int T>
+static void stage_launch(const DevGrid& g, int stage, const StageArgs& a, cudaStream_t s) {
+  dim3 grid = stage_grid(g, T), block(T);
   switch (stage) {
-    case 1: stage_kernel<D, S, M, 1><<<grid, block, 0, s>>>(g, a); break;
-    case 2: stage_kernel<D, S, M, 2><<<grid, block, 0, s>>>(g, a); break;
-    default: stage_kernel<D, S, M, 3><<<grid, block, 0, s>>>(g, a); break;
+    case 1: stage_kernel<D, S, M, 1, T><<<grid, block, 0, s>>>(g, a); break;
+    case 2: stage_kernel<D, S, M, 2, T><<<grid, block, 0, s>>>(g, a); break;
+    default: stage_kernel<D, S, M, 3, T><<<grid, block, 0, s>>>(g, a); break;
+  }
+}
+
+template <int D, int S, int M>
+static cudaError_t stage_dispatch(const DevGrid& g, int stage, const StageArgs& a, int threads,
+                                  cudaStream_t s) {
+  switch (threads) {
+    case 128: stage_launch<D, S, M, 128>(g, stage, a, s); break;
+    case 512: stage_launch<D, S, M, 512>(g, stage, a, s); break;
+    default: stage_launch<D, S, M, 256>(g, stage, a, s); break;
   }
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
@@ -210,11 +220,11 @@ static cudaError_t stage_dispatch(const DevGrid& g, int stage, const StageArgs& 
 
 template <int D, int M>
 static cudaError_t stage_by_scheme(const DevGrid& g, int scheme, int stage, const StageArgs& a,
-                                   cudaStream_t s) {
+                                   int threads, cudaStream_t s) {
   switch (scheme) {
-    case 1: return stage_dispatch<D, 1, M>(g, stage, a, s);
-    case 2: return stage_dispatch<D, 2, M>(g, stage, a, s);
-    case 5: return stage_dispatch<D, 5, M>(g, stage, a, s);
+    case 1: return stage_dispatch<D, 1, M>(g, stage, a, threads, s);
+    case 2: return stage_dispatch<D, 2, M>(g, stage, a, threads, s);
+    case 5: return stage_dispatch<D, 5, M>(g, stage, a, threads, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -227,16 +237,17 @@ bool stage_supported(int model, int ndim, int scheme) {
   return false;
 }
 
-cudaError_t launch_stage(const DevGrid& g, int scheme, int stage, const StageArgs& a, cudaStream_t s) {
+cudaError_t launch_stage(const DevGrid& g, int scheme, int stage, const StageArgs& a, cudaStream_t s,
+                         int threads) {
   switch (g.model) {
-    case hjd::M_QUAD_Z: return stage_by_scheme<2, hjd::M_QUAD_Z>(g, scheme, stage, a, s);
-    case hjd::M_QUAD_X4: return stage_by_scheme<4, hjd::M_QUAD_X4>(g, scheme, stage, a, s);
+    case hjd::M_QUAD_Z: return stage_by_scheme<2, hjd::M_QUAD_Z>(g, scheme, stage, a, threads, s);
+    case hjd::M_QUAD_X4: return stage_by_scheme<4, hjd::M_QUAD_X4>(g, scheme, stage, a, threads, s);
     default:
       switch (g.ndim) {
-        case 1: return stage_by_scheme<1, hjd::M_DRIFT>(g, scheme, stage, a, s);
-        case 2: return stage_by_scheme<2, hjd::M_DRIFT>(g, scheme, stage, a, s);
-        case 3: return stage_by_scheme<3, hjd::M_DRIFT>(g, scheme, stage, a, s);
-        case 4: return stage_by_scheme<4, hjd::M_DRIFT>(g, scheme, stage, a, s);
+        case 1: return stage_by_scheme<1, hjd::M_DRIFT>(g, scheme, stage, a, threads, s);
+        case 2: return stage_by_scheme<2, hjd::M_DRIFT>(g, scheme, stage, a, threads, s);
+        case 3: return stage_by_scheme<3, hjd::M_DRIFT>(g, scheme, stage, a, threads, s);
+        case 4: return stage_by_scheme<4, hjd::M_DRIFT>(g, scheme, stage, a, threads, s);
       }
   }
   return cudaErrorInvalidValue;

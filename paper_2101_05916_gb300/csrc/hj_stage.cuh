@@ -77,6 +77,15 @@ __device__ __forceinline__ unsigned stage_point(const DevGrid& g, const StageArg
     float r = fabsf(wn - sv);
     a.snap[p] = wn;
     if (a.band > 0.f && fminf(fabsf(wn), fabsf(sv)) > a.band) r = 0.f;
+    if (a.margin > 0) {
+      // only faces of unconstrained axes: on a constrained axis the margin l
+      // decides the value next to the face
+#pragma unroll
+      for (int d = 0; d < D; ++d)
+        if (!((g.con_kind == C_BOX) && ((g.con_mask >> d) & 1u)) &&
+            (idx[d] < a.margin || idx[d] > g.n[d] - 1 - a.margin))
+          r = 0.f;
+    }
     if (wn != wn) r = wn;  // NaN always reaches the stop test
     return __float_as_uint(r);
   }

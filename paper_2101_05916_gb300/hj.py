@@ -46,7 +46,8 @@ class hj_solve_opts(ctypes.Structure):
                 ("tol", ctypes.c_double), ("check_dt", ctypes.c_double),
                 ("max_steps", ctypes.c_longlong), ("fixed_steps", ctypes.c_longlong),
                 ("max_wall_ms", ctypes.c_double), ("clamp", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("band", ctypes.c_double)]
+                ("use_graph", ctypes.c_int), ("band", ctypes.c_double),
+                ("autotune", ctypes.c_int), ("band_margin", ctypes.c_int)]
 
 
 class hj_solve_stats(ctypes.Structure):
@@ -100,6 +101,7 @@ SIGNATURES = {
     "hj_query_value": (_i, [_vp, _i, _P(_d), _P(_d)]),
     "hj_query_gradient": (_i, [_vp, _i, _P(_d), _P(_d)]),
     "hj_alpha": (_i, [_vp, _P(_d)]),
+    "hj_autotune": (_i, [_vp, _i, _P(_i)]),
     "hj_grid_points": (_ll, [_vp]),
     "hj_last_error": (ctypes.c_char_p, []),
     "hj_kernel_launches": (ctypes.c_ulonglong, []),
@@ -208,9 +210,10 @@ def hj_set_disturbance_bound(g: int, d_lo: Sequence[float], d_hi: Sequence[float
 def make_opts(scheme: int = HJ_WENO5, cfl: float = 0.5, dt: float = 0.0, tol: float = 1e-4,
               check_dt: float = 0.1, max_steps: int = 1000000, fixed_steps: int = 0,
               max_wall_ms: float = 0.0, clamp: int = HJ_CLAMP_VI,
-              use_graph: bool = True, band: float = 0.0) -> hj_solve_opts:
+              use_graph: bool = True, band: float = 0.0,
+              autotune: bool = False, band_margin: int = 0) -> hj_solve_opts:
     return hj_solve_opts(scheme, cfl, dt, tol, check_dt, max_steps, fixed_steps, max_wall_ms,
-                         clamp, 1 if use_graph else 0, band)
+                         clamp, 1 if use_graph else 0, band, 1 if autotune else 0, band_margin)
 
 
 def hj_solve(g: int, mode: int = HJ_COLD, opts: Optional[hj_solve_opts] = None,
@@ -298,6 +301,12 @@ def hj_query_gradient(g: int, xs, ndim: int) -> np.ndarray:
     out = np.zeros_like(a)
     _check(lib().hj_query_gradient(g, a.shape[0], p, out.ctypes.data_as(_P(_d))))
     return out
+
+
+def hj_autotune(g: int, scheme: int = HJ_WENO5) -> int:
+    t = ctypes.c_int()
+    _check(lib().hj_autotune(g, int(scheme), ctypes.byref(t)))
+    return t.value
 
 
 def hj_alpha(g: int, ndim: int) -> np.ndarray:

@@ -35,15 +35,10 @@ def shard(trace: Sequence, rank: int, world: int) -> List:
 
 
 def solve_opts_for(req) -> Dict:
-    """Stop rule per subsystem type.  2-D z: full-grid L-inf test, VI clamp.
-    4-D x/y: monotone clamp min(W3, l, W_prev) and the band |W| <= 0.5, the
-    combination that converges on every seeded request (WENO5 with the VI
-    clamp keeps cycling at grid faces that the zero level set touches)."""
-    if req.spec.ndim == 4:
-        return dict(scheme=req.scheme, band=0.5, clamp=hj.HJ_CLAMP_MONOTONE, max_steps=200000,
-                    max_wall_ms=300000.0)
-    return dict(scheme=req.scheme, band=0.0, clamp=hj.HJ_CLAMP_VI, max_steps=200000,
-                max_wall_ms=300000.0)
+    """Stop rule per subsystem type (see scenarios.X4_OPTS / Z_OPTS)."""
+    from .scenarios import X4_OPTS, Z_OPTS
+    base = X4_OPTS if req.spec.ndim == 4 else Z_OPTS
+    return dict(base, scheme=req.scheme)
 
 
 def replay_server(trace: Sequence, budget_bytes: int = 40 << 30, max_active: int = 64,

@@ -177,6 +177,21 @@ def test_x13_converged_parity_monotone_band(hj):
     assert_parity(Wg, Wo, spec)
 
 
+def test_x17_converged_parity_vi_band_margin(hj):
+    """VI clamp with the band stop test skipping a 3-cell layer at the faces
+    of the free axes (v, theta, omega), both sides."""
+    spec = wl.quad_x4(17, 0.8, 4.0, shift=0.5)
+    kw = dict(scheme=5, tol=1e-4, clamp=0, band=0.5, band_margin=3)
+    Wo, sto = oracle.solve(spec, max_steps=60000, **kw)
+    g = hj.Grid.from_spec(spec)
+    st = g.solve(hj.HJ_COLD, **kw)
+    Wg = g.value()
+    g.close()
+    assert st["converged"] and sto["converged"]
+    assert abs(st["windows"] - sto["windows"]) <= 3, (st["windows"], sto["windows"])
+    assert_parity(Wg, Wo, spec)
+
+
 def test_warm_start_reaches_cold_fixed_point(hj):
     """Sec. III-B on the GPU: the b = 0.5 result warm-starts the b = 1.0 solve,
     which lands on the cold b = 1.0 fixed point in fewer steps."""
@@ -435,3 +450,26 @@ def test_kernel_launch_counter_moves(hj):
     g.solve(hj.HJ_COLD, scheme=2, fixed_steps=4)
     g.close()
     assert hj.hj_kernel_launches() - before >= 12
+
+
+def test_autotune_keeps_value_and_results(hj):
+    """The launch-shape autotuner only changes threads per block: W is left
+    as it was, and solves after tuning give bit-identical results."""
+    spec = wl.quad_x4(23, 0.5)
+    g = hj.Grid.from_spec(spec)
+    g.solve(hj.HJ_COLD, scheme=5, fixed_steps=3)
+    before = g.value()
+    t = hj.hj_autotune(g.handle, hj.HJ_WENO5)
+    assert t in (128, 256, 512)
+    assert np.array_equal(g.value(), before)
+    st1 = g.solve(hj.HJ_COLD, scheme=5, fixed_steps=7)
+    W1 = g.value()
+    g.close()
+    g2 = hj.Grid.from_spec(spec)
+    g2.solve(hj.HJ_COLD, scheme=5, fixed_steps=7, autotune=True)
+    W2 = g2.value()
+    g2.close()
+    assert np.array_equal(W1, W2)
+    dt = oracle.cfl_dt(spec)
+    Wo, _ = oracle.solve(spec, scheme=5, dt=st1["dt"], fixed_steps=7)
+    assert_parity(W1, Wo, spec)

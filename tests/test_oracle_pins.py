@@ -316,6 +316,21 @@ def test_band_stop_test_reduces_to_full_test_and_never_stops_later():
     assert np.abs(Wn - Wc)[near].max() < 5e-3
 
 
+def test_band_margin_skips_faces_of_free_axes_only():
+    """The margin removes nodes next to faces of unconstrained axes from the
+    stop test: on the 2-D z grid only the vz axis is free, so a margin wider
+    than half that axis empties the test (it stops after one window), while
+    a zero margin is the plain band test."""
+    s = wl.quad_z(41, 0.5)
+    W0, st0 = oracle.solve(s, scheme=2, tol=1e-4, band=0.5)
+    W1, st1 = oracle.solve(s, scheme=2, tol=1e-4, band=0.5, band_margin=0)
+    assert st0["steps"] == st1["steps"]
+    W2, st2 = oracle.solve(s, scheme=2, tol=1e-4, band=0.5, band_margin=21)
+    assert st2["windows"] == 1 and st2["residual"] == 0.0
+    W3, st3 = oracle.solve(s, scheme=2, tol=1e-4, band=0.5, band_margin=3)
+    assert st3["converged"] and st3["steps"] <= st0["steps"]
+
+
 def test_no_motion_is_already_converged():
     s = wl.drift((11,), 1.0, 0.0, wl.CON_BOX, r=0.5)
     W, st = oracle.solve(s, scheme=2)
