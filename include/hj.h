@@ -250,6 +250,11 @@ typedef struct {
   int mode;                     /* HJ_COLD, or HJ_WARM = use the key's resident prior when exact */
   long long key;                /* subsystem identity for residency; 0 = none                  */
   hj_solve_opts opts;
+  int coarse_n;                 /* >= 3: coarse initialisation (Sec. III-C).  The request first */
+                                /* solves on a grid of coarse_n nodes per axis over the same    */
+                                /* box, then migrates that value to its own grid (hj_prolong)   */
+                                /* and finishes with a warm solve there.  Exact or conservative */
+                                /* (Sec. III-B), usually far fewer fine steps.  0: off.         */
 } hj_request;
 
 typedef struct {

@@ -27,6 +27,9 @@
 namespace hjb {
 
 constexpr int kThreads = hjk::kStageThreads;
+// Grids with at least this many nodes launch alone (about 1.5 waves of the
+// 152 SMs at 8 blocks of 256 threads); smaller grids of one kind are fused.
+constexpr int kSoloNodes = 1 << 20;
 
 __host__ __device__ constexpr int kind_code(int model, int ndim, int scheme) {
   return model * 100 + ndim * 10 + scheme;
@@ -264,7 +267,17 @@ hj_status Runner::rebuild() {
     Slot& s = slots_[k];
     hj_grid g = s.g;
     if (groups_.empty() || groups_.back().kind != by_kind[j].first ||
-        groups_.back().pack.count == kPackItems) {
+        groups_.back().pack.count == kPackItems ||
+        groups_.back().pack.items[0].g.npts >= kSoloNodes) {
+      groups_.emplace_back();
+      Group& ng = groups_.back();
+      std::memset(&ng.pack, 0, sizeof(ng.pack));
+      ng.kind = by_kind[j].first;
+      ng.blocks = 0;
+    }
+    // a grid that fills the GPU by itself gains nothing from fusion; it keeps
+    // its own single-grid launch (a group of one)
+    if (g->npts >= kSoloNodes && groups_.back().pack.count > 0) {
       groups_.emplace_back();
       Group& ng = groups_.back();
       std::memset(&ng.pack, 0, sizeof(ng.pack));

@@ -6,7 +6,9 @@
 // Here one worker thread owns a batch Runner.  Each loop it:
 //   1. admits queued requests (arrival order, first fit) while active slots
 //      and the HBM budget allow; a request with a dominated resident prior
-//      for its key warm-starts from it, every other request starts cold;
+//      for its key warm-starts from it, every other request starts cold; a
+//      request with coarse initialisation (Sec. III-C) first steps a coarse
+//      grid, is migrated to its own grid, and then steps that grid warm;
 //   2. advances all admitted grids by one round (fused launches, per-grid
 //      stop decisions on the device);
 //   3. retires finished grids, records latency, and makes each converged
@@ -39,8 +41,13 @@ enum ReqState { Q_QUEUED = 0, Q_RUNNING = 1, Q_DONE = 2 };
 struct Req {
   long long ticket = 0;
   hj_request r{};
-  size_t bytes = 0;
+  size_t bytes = 0;          // fine grid bytes (plus the coarse grid while it lives)
+  size_t coarse_bytes = 0;
   long long npts = 0;
+  long long coarse_npts = 0;
+  int phase = 0;             // 0: single solve; 1: coarse phase; 2: fine phase after migration
+  hj_grid gc = nullptr;      // coarse grid of the coarse phase
+  long long coarse_steps = 0;
   Clock::time_point t_submit, t_done;
   int state = Q_QUEUED;
   hj_grid g = nullptr;
@@ -205,6 +212,40 @@ void hj_server_s::admit_locked(std::vector<long long>& admitted) {
     hj_grid g = nullptr;
     hj_status s = make_grid(q.r, stream, &g);
     int mode = HJ_COLD;
+    bool coarse_first = q.coarse_npts > 0;
+    if (s == HJ_OK && coarse_first) {
+      // coarse initialisation: the coarse grid steps first; the fine grid
+      // waits for the migrated value
+      hj_request rc = q.r;
+      for (int i = 0; i < rc.ndim; ++i) rc.n[i] = rc.coarse_n;
+      s = make_grid(rc, stream, &q.gc);
+      int slot = -1;
+      if (s == HJ_OK) s = runner->add(q.gc, HJ_COLD, q.r.opts, &slot);
+      if (s != HJ_OK) {
+        if (q.gc) hj_grid_destroy(q.gc);
+        q.gc = nullptr;
+        hj_grid_destroy(g);
+        q.state = Q_DONE;
+        q.result = s;
+        q.t_done = Clock::now();
+        st.failed++;
+        it = queue.erase(it);
+        cv_done.notify_all();
+        continue;
+      }
+      q.g = g;
+      q.slot = slot;
+      q.phase = 1;
+      q.state = Q_RUNNING;
+      used += q.bytes;
+      active_nodes += q.coarse_npts;
+      st.peak_bytes = std::max<long long>(st.peak_bytes, (long long)used);
+      st.admitted++;
+      st.cold_starts++;
+      admitted.push_back(q.ticket);
+      it = queue.erase(it);
+      continue;
+    }
     if (s == HJ_OK && q.r.mode == HJ_WARM && q.r.key != 0) {
       auto rk = resident_of_key.find(q.r.key);
       if (rk != resident_of_key.end()) {
@@ -272,6 +313,37 @@ void hj_server_s::run() {
     auto now = Clock::now();
     for (auto it = running.begin(); it != running.end();) {
       Req& q = reqs[*it];
+      if (rs == HJ_OK && q.phase == 1 && runner->finished(q.slot)) {
+        // coarse phase done: migrate to the fine grid and step it from there
+        hj_solve_stats cs{};
+        hj_status r = runner->collect(q.slot, &cs);
+        q.coarse_steps = cs.steps;
+        int slot = -1;
+        if (r == HJ_OK || r == HJ_ERR_NOT_CONVERGED) r = hj_prolong(q.gc, q.g);
+        if (r == HJ_OK) r = runner->add(q.g, HJ_WARM, q.r.opts, &slot);
+        hj_grid_destroy(q.gc);
+        q.gc = nullptr;
+        used -= q.coarse_bytes;
+        q.bytes -= q.coarse_bytes;
+        active_nodes -= q.coarse_npts;
+        st.updates += (double)q.coarse_npts * (double)cs.steps;
+        if (r == HJ_OK) {
+          q.slot = slot;
+          q.phase = 2;
+          active_nodes += q.npts;
+          ++it;
+          continue;
+        }
+        q.result = r;
+        q.state = Q_DONE;
+        q.t_done = now;
+        q.last_use = now;
+        t_last_done = now;
+        st.failed++;
+        latencies.push_back(ms_since(q.t_submit, now));
+        it = running.erase(it);
+        continue;
+      }
       if (rs != HJ_OK || runner->finished(q.slot)) {
         hj_solve_stats s{};
         hj_status r = rs != HJ_OK ? rs : runner->collect(q.slot, &s);
@@ -282,7 +354,13 @@ void hj_server_s::run() {
         q.t_done = now;
         q.last_use = now;
         t_last_done = now;
-        active_nodes -= q.npts;
+        active_nodes -= q.phase == 1 ? q.coarse_npts : q.npts;
+        if (q.gc) {
+          hj_grid_destroy(q.gc);
+          q.gc = nullptr;
+          used -= q.coarse_bytes;
+          q.bytes -= q.coarse_bytes;
+        }
         latencies.push_back(s.wall_ms);
         // grid-point updates count for every request that stepped, converged or not
         st.updates += (double)q.npts * (double)s.steps;
@@ -380,7 +458,17 @@ hj_status hj_server_submit(hj_server s, const hj_request* r, long long* ticket) 
     if (npts >= (1ll << 31)) return hja::fail(HJ_ERR_ARG, "grid too large");
   }
   if (r->mode != HJ_COLD && r->mode != HJ_WARM) return hja::fail(HJ_ERR_ARG, "bad mode");
-  size_t bytes = grid_bytes(npts);
+  long long cnpts = 0;
+  if (r->coarse_n != 0) {
+    if (r->coarse_n < 3) return hja::fail(HJ_ERR_ARG, "coarse_n must be 0 or >= 3");
+    cnpts = 1;
+    for (int i = 0; i < r->ndim; ++i) {
+      if (r->coarse_n > r->n[i]) return hja::fail(HJ_ERR_ARG, "coarse_n exceeds axis %d", i);
+      cnpts *= r->coarse_n;
+    }
+  }
+  size_t cbytes = cnpts ? grid_bytes(cnpts) : 0;
+  size_t bytes = grid_bytes(npts) + cbytes;
   std::lock_guard<std::mutex> lk(s->mu);
   if (bytes > s->budget) {
     s->st.rejected++;
@@ -390,7 +478,9 @@ hj_status hj_server_submit(hj_server s, const hj_request* r, long long* ticket) 
   q.ticket = s->next_ticket++;
   q.r = *r;
   q.bytes = bytes;
+  q.coarse_bytes = cbytes;
   q.npts = npts;
+  q.coarse_npts = cnpts;
   q.t_submit = Clock::now();
   q.last_use = q.t_submit;
   if (!s->first_submit_seen) {

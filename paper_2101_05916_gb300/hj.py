@@ -69,7 +69,7 @@ class hj_request(ctypes.Structure):
                 ("hi", _d * HJ_MAX_DIM), ("model", _i), ("params", _d * 8), ("nparams", _i),
                 ("d_lo", _d * HJ_MAX_DIM), ("d_hi", _d * HJ_MAX_DIM), ("nd", _i),
                 ("con_ball", _i), ("con_a", _d * HJ_MAX_DIM), ("con_b", _d * HJ_MAX_DIM),
-                ("mode", _i), ("key", _ll), ("opts", hj_solve_opts)]
+                ("mode", _i), ("key", _ll), ("opts", hj_solve_opts), ("coarse_n", _i)]
 
 
 class hj_server_stats(ctypes.Structure):
@@ -336,9 +336,11 @@ def hj_solve_fixed_static(spec, W, mode: int = HJ_COLD, scheme: int = HJ_WENO5,
     del keep
 
 
-def make_request(spec, mode: int = HJ_COLD, key: int = 0, **opts) -> hj_request:
-    """An hj_request for a workloads.ProblemSpec."""
+def make_request(spec, mode: int = HJ_COLD, key: int = 0, coarse_n: int = 0,
+                 **opts) -> hj_request:
+    """An hj_request for a workloads.ProblemSpec (coarse_n > 0: coarse initialisation)."""
     r = hj_request()
+    r.coarse_n = int(coarse_n)
     r.ndim = spec.ndim
     for i in range(spec.ndim):
         r.n[i] = int(spec.n[i])

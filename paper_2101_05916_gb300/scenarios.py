@@ -3,10 +3,10 @@
 Each scenario runs the paper's accelerations against the plain way of
 solving, through the same C ABI:
 
-* decomposed_update (Sec. III-A + III-B): the x, y and z subsystems of the
-  10-D quadcopter.  After every new wind bound they are solved as one batch,
-  warm-started from the previous fixed point.  The plain way is three cold
-  single-grid solves, one after another.
+* decomposed_update (Sec. III-A, III-B, III-C): the x, y and z subsystems of
+  the 10-D quadcopter, updated after every new wind bound.  Variants: one
+  warm-started batch; or a coarse warm batch, migration, and a fine batch.
+  The plain way is three cold single-grid solves, one after another.
 * adaptive_grid (Sec. III-C): a coarse cold solve, migration to the fine
   grid, and a warm fine solve.  The plain way is a cold fine solve.
 * serving: a seeded request trace replayed through the continuous-batching
@@ -47,58 +47,85 @@ def _sync():
     torch.cuda.synchronize()
 
 
-def decomposed_update(n4: int = 61, n2: int = 201,
-                      bounds: Sequence[float] = wl.CONFIG2_BOUNDS) -> Dict:
-    """Wind bound raised in sequence; every update of {x, y, z} is one batch
-    warm-started from the previous fixed points (a larger wind bound with the
-    same constraint keeps the prior dominating, so the warm start is exact).
-    Baseline: cold single-grid solves of x, y and z in turn."""
-    specs = wl.config2(n4, n2)
-    grids = [hj.Grid.from_spec(s) for s in specs]
+def _batch(grids, modes, specs):
     opts = [hj.make_opts(**_opts_for(s)) for s in specs]
-    batched: List[Dict] = []
+    _sync()
+    t0 = time.perf_counter()
+    rc, sts, stats = hj.hj_solve_batch([g.handle for g in grids], modes, opts)
+    _sync()
+    return 1e3 * (time.perf_counter() - t0), [s["steps"] for s in stats], sts
+
+
+def decomposed_update(n4: int = 61, n2: int = 201, nc4: int = 31, nc2: int = 101,
+                      bounds: Sequence[float] = wl.CONFIG2_BOUNDS) -> Dict:
+    """The wind bound is raised in sequence.  Every update of {x, y, z} is
+    solved three ways, as in the three columns of the paper's Table I:
+
+    * plain: cold single-grid solves of x, y and z in turn (decomposition
+      only);
+    * warm: one batch of the three grids, warm-started from the previous fixed
+      points (decomposition + warm start).  A larger bound with the same
+      constraint keeps the prior dominating;
+    * new: the coarse grids (x, y at nc4^4, z at nc2^2) solved as one batch,
+      warm from their previous fixed points, then migrated to the fine grids,
+      which are solved as one batch from the migrated values (decomposition +
+      warm start + coarse initialization, Sec. III-C).
+    """
+    specs = wl.config2(n4, n2)
+    coarse_specs = wl.config2(nc4, nc2)
+    warm_grids = [hj.Grid.from_spec(s) for s in specs]
+    fine = [hj.Grid.from_spec(s) for s in specs]
+    coarse = [hj.Grid.from_spec(s) for s in coarse_specs]
+    rows = []
     for k, b in enumerate(bounds):
-        for g, s in zip(grids, specs):
+        for g, s in zip(warm_grids + fine, specs + specs):
             g.set_disturbance_bound([-b] * len(s.d_lo), [b] * len(s.d_hi))
-        modes = [hj.HJ_COLD if k == 0 else hj.HJ_WARM] * len(grids)
+        for g, s in zip(coarse, coarse_specs):
+            g.set_disturbance_bound([-b] * len(s.d_lo), [b] * len(s.d_hi))
+        first = k == 0
+        w_ms, w_steps, w_sts = _batch(warm_grids, [hj.HJ_COLD if first else hj.HJ_WARM] * 3, specs)
+        c_ms, c_steps, c_sts = _batch(coarse, [hj.HJ_COLD if first else hj.HJ_WARM] * 3,
+                                      coarse_specs)
         _sync()
         t0 = time.perf_counter()
-        rc, sts, stats = hj.hj_solve_batch([g.handle for g in grids], modes, opts)
+        for gc, gf in zip(coarse, fine):
+            hj.prolong(gc, gf)
         _sync()
-        ms = 1e3 * (time.perf_counter() - t0)
-        batched.append(dict(bound=b, ms=ms, steps=[s["steps"] for s in stats],
-                            statuses=sts, mode="cold" if k == 0 else "warm"))
-    safe = [float(np.mean(g.value() >= 0)) for g in grids]
-    finals = [g.value() for g in grids]
-    for g in grids:
+        p_ms = 1e3 * (time.perf_counter() - t0)
+        f_ms, f_steps, f_sts = _batch(fine, [hj.HJ_WARM] * 3, specs)
+        row = dict(bound=b, warm_ms=w_ms, warm_steps=w_steps, new_ms=c_ms + p_ms + f_ms,
+                   new_coarse_steps=c_steps, new_fine_steps=f_steps,
+                   statuses=[int(x) for x in w_sts + c_sts + f_sts])
+        if not first:
+            total, steps, outs = 0.0, [], []
+            for s in specs:
+                g = hj.Grid.from_spec(s.with_bound(b))
+                _sync()
+                t1 = time.perf_counter()
+                rc, st = hj.hj_solve(g.handle, hj.HJ_COLD, hj.make_opts(**_opts_for(s)),
+                                     raise_on_error=False)
+                _sync()
+                total += 1e3 * (time.perf_counter() - t1)
+                steps.append(st["steps"])
+                outs.append(g.value())
+                g.close()
+            row.update(plain_ms=total, plain_steps=steps)
+            row["sign_agreement_warm"] = [float(np.mean((g.value() >= 0) == (c >= 0)))
+                                          for g, c in zip(warm_grids, outs)]
+            row["sign_agreement_new"] = [float(np.mean((g.value() >= 0) == (c >= 0)))
+                                         for g, c in zip(fine, outs)]
+        rows.append(row)
+    for g in warm_grids + fine + coarse:
         g.close()
-    plain: List[Dict] = []
-    for b in bounds[1:]:
-        total, steps, rcs = 0.0, [], []
-        outs = []
-        for s in specs:
-            g = hj.Grid.from_spec(s.with_bound(b))
-            _sync()
-            t0 = time.perf_counter()
-            rc, st = hj.hj_solve(g.handle, hj.HJ_COLD, hj.make_opts(**_opts_for(s)),
-                                 raise_on_error=False)
-            _sync()
-            total += 1e3 * (time.perf_counter() - t0)
-            steps.append(st["steps"])
-            rcs.append(rc)
-            outs.append(g.value())
-            g.close()
-        plain.append(dict(bound=b, ms=total, steps=steps, statuses=rcs))
-    # the last warm batch against the last cold solves
-    sign_agree = [float(np.mean((a >= 0) == (c >= 0))) for a, c in zip(finals, outs)]
-    upd = [r["ms"] for r in batched[1:]]
-    base = [r["ms"] for r in plain]
-    return dict(grids=[s.name + "%s" % (s.n,) for s in specs], batched=batched, plain=plain,
-                update_ms_p50=float(np.percentile(upd, 50)),
-                update_ms_max=float(np.max(upd)),
-                plain_ms_p50=float(np.percentile(base, 50)),
-                plain_ms_max=float(np.max(base)),
-                safe_fraction=safe, sign_agreement_last_update=sign_agree)
+    upd = rows[1:]
+
+    def p50(key):
+        return float(np.percentile([r[key] for r in upd], 50))
+
+    return dict(grids=[s.name + "%s" % (s.n,) for s in specs],
+                coarse_grids=[s.name + "%s" % (s.n,) for s in coarse_specs], updates=rows,
+                plain_ms_p50=p50("plain_ms"), warm_ms_p50=p50("warm_ms"), new_ms_p50=p50("new_ms"),
+                speedup_new_vs_plain=p50("plain_ms") / p50("new_ms"))
 
 
 def adaptive_grid(nc: int = 31, nf: int = 81, b: float = 1.0,
@@ -161,14 +188,17 @@ def load_reference(path: str) -> Optional[Dict]:
     return dict(idx=a[:, :4].astype(np.int64), W=a[:, 4])
 
 
-def serving(count: int = 16) -> Dict:
+def serving(count: int = 16, coarse_4d: int = 13) -> Dict:
     """The first `count` requests of the seeded serving trace through the
-    server (default policy) and through one-at-a-time cold solves."""
+    server (default policy), through the server with coarse initialisation of
+    the 4-D requests, and through one-at-a-time cold solves."""
     trace = wl.serving_trace()[:count]
     a = serve.replay_server(trace)
+    c = serve.replay_server(trace, coarse_4d=coarse_4d)
     b = serve.replay_fifo_cold(trace)
     keep = ("p50_ms", "p99_ms", "mean_ms", "wall_s", "updates_per_s")
     return dict(requests=count,
                 served={k: a[k] for k in keep},
+                served_coarse_init={k: c[k] for k in keep},
                 plain_cold={k: b[k] for k in keep},
-                all_converged=all(s == 0 for s in a["statuses"] + b["statuses"]))
+                all_converged=all(s == 0 for s in a["statuses"] + b["statuses"] + c["statuses"]))

@@ -207,3 +207,37 @@ def test_shortest_first_policy_with_node_cap(hj):
     with pytest.raises(hj.HJError):
         hj.hj_server_set_policy(s2, 7, 0)
     hj.hj_server_destroy(s2)
+
+
+def test_coarse_initialisation_in_the_server(hj):
+    """A request with coarse_n runs coarse solve -> migration -> warm fine
+    solve inside the server: bit-identical to doing those three calls by
+    hand, and the same safe set as a cold fine solve up to the coarse
+    start's conservatism (Sec. III-B/C)."""
+    from paper_2101_05916_gb300 import scenarios
+    spec = wl.quad_x4(25, 0.7)
+    opts = dict(scenarios.X4_OPTS, max_wall_ms=0.0)
+    s = hj.hj_server_create(4 << 30, 8)
+    req = hj.make_request(spec, hj.HJ_COLD, 0, coarse_n=13, **opts)
+    rc, st, W = fetch(hj, s, hj.hj_server_submit(s, req), spec)
+    stats = hj.hj_server_get_stats(s)
+    hj.hj_server_destroy(s)
+    assert rc == hj.HJ_OK and stats["completed"] == 1
+    gc, gf = hj.Grid.from_spec(wl.quad_x4(13, 0.7)), hj.Grid.from_spec(spec)
+    gc.solve(hj.HJ_COLD, **opts)
+    hj.prolong(gc, gf)
+    stw = gf.solve(hj.HJ_WARM, **opts)
+    Wm = gf.value()
+    stc = gf.solve(hj.HJ_COLD, **opts)
+    Wc = gf.value()
+    gc.close()
+    gf.close()
+    assert st["steps"] == stw["steps"]
+    assert np.array_equal(W, Wm)
+    assert np.mean((W >= 0) == (Wc >= 0)) >= 0.99
+    with pytest.raises(hj.HJError):
+        s2 = hj.hj_server_create(1 << 30, 2)
+        try:
+            hj.hj_server_submit(s2, hj.make_request(spec, 0, 0, coarse_n=2, **opts))
+        finally:
+            hj.hj_server_destroy(s2)
