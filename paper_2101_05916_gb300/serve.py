@@ -111,3 +111,35 @@ def replay_fifo_cold(trace: Sequence, time_scale: float = 1.0, stream=None) -> D
     return dict(p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
                 mean_ms=float(np.mean(lat)), wall_s=wall, statuses=statuses, updates=updates,
                 updates_per_s=updates / max(wall, 1e-9), latencies_ms=lat)
+
+
+def main(argv=None) -> None:
+    """python -m paper_2101_05916_gb300.serve [--requests K] [--coarse N] [--no-plain]
+
+    Replays the first K requests of the seeded serving trace through the
+    server and through one-at-a-time cold solves; prints one JSON line."""
+    import argparse
+    import json
+
+    from . import build, workloads as wl
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--requests", type=int, default=256)
+    ap.add_argument("--coarse", type=int, default=0,
+                    help="coarse initialisation of the 4-D requests (nodes per axis, 0 = off)")
+    ap.add_argument("--no-plain", action="store_true")
+    a = ap.parse_args(argv)
+    build.build()
+    trace = wl.serving_trace()[:a.requests]
+    keep = ("p50_ms", "p99_ms", "mean_ms", "wall_s", "updates_per_s", "updates")
+    s = replay_server(trace, coarse_4d=a.coarse)
+    out = {"requests": len(trace), "coarse_4d": a.coarse, "served": {k: s[k] for k in keep},
+           "server_stats": s["server"], "served_statuses": sorted(set(s["statuses"]))}
+    if not a.no_plain:
+        p = replay_fifo_cold(trace)
+        out["plain_cold"] = {k: p[k] for k in keep}
+        out["plain_statuses"] = sorted(set(p["statuses"]))
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
