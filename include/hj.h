@@ -330,9 +330,9 @@ hj_status hj_server_set_policy(hj_server s, int order, long long max_active_node
  *
  * Where the scratch lives: the working memory is one file-scope device
  * array, shared by every call in the process.  It holds the Lax-Friedrichs
- * coefficient accumulator, the g tan(th) table and the two Runge-Kutta stage
- * fields.  Every GPU that loads the library holds the array (about 32 MiB)
- * until the process exits.
+ * coefficient accumulator, the g tan(th) table, a guarded working copy of W
+ * and the two Runge-Kutta stage fields.  Every GPU that loads the library
+ * holds the array (about 48 MiB) until the process exits.
  *
  * Limits: at most HJ_STATIC_MAX_POINTS nodes and at most HJ_STATIC_MAX_AXIS
  * nodes on the theta axis of HJ_QUAD_X4.  Larger problems fail with

@@ -324,10 +324,7 @@ void hj_grid_destroy(hj_grid g) {
     DeviceGuard dg(g->device);
     if (g->stream) cudaStreamSynchronize(g->stream);
     drop_graph(g);
-    cudaFree(g->W);
-    cudaFree(g->A);
-    cudaFree(g->B);
-    cudaFree(g->snap);
+    for (int i = 0; i < 4; ++i) cudaFree(g->raw[i]);
     cudaFree(g->tab);
     cudaFree(g->dscal);
     cudaFree(g->qbuf);
@@ -369,13 +366,20 @@ hj_status hj_grid_create(hj_grid* out, int ndim, const int* n, const double* lo,
     g->h[i] = (hi[i] - lo[i]) / (double)(n[i] - 1);
   }
   g->stream = (cudaStream_t)cuda_stream;
-  size_t bytes = (size_t)npts * sizeof(float);
+  // each field: guard floats, the nodes, guard floats
+  size_t bytes = ((size_t)npts + 2 * kGuard) * sizeof(float);
   bytes = (bytes + 255) & ~(size_t)255;
   cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = cudaMalloc(&g->W, bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&g->A, bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&g->B, bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&g->snap, bytes);
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
+    e = cudaMalloc(&g->raw[i], bytes);
+    if (e == cudaSuccess) e = cudaMemset(g->raw[i], 0, bytes);
+  }
+  if (e == cudaSuccess) {
+    g->W = g->raw[0] + kGuard;
+    g->A = g->raw[1] + kGuard;
+    g->B = g->raw[2] + kGuard;
+    g->snap = g->raw[3] + kGuard;
+  }
   if (e == cudaSuccess) e = cudaMalloc(&g->dscal, 64 * sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMallocHost(&g->hscal, 64 * sizeof(unsigned));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);

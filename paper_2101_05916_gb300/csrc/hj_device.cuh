@@ -212,6 +212,35 @@ __device__ __forceinline__ void load_line(const float* __restrict__ src, int p, 
   }
 }
 
+// The same line along the fastest axis (stride 1), without branches.  The
+// 2R+1 values are loaded unclamped at immediate offsets.  Near a row end some
+// of them come from the neighbouring row, or from the guard floats every
+// field carries before its first and after its last node.  Those slots are
+// then replaced, with selects, by the linear continuation of the row through
+// its two outermost nodes.  Nearly every warp holds a lane within R nodes of
+// a row end, so a branch here would run both paths in almost every warp.
+template <int R>
+__device__ __forceinline__ void load_fast_line(const float* __restrict__ src, int p, int i, int n,
+                                               float (&v)[2 * R + 1]) {
+#pragma unroll
+  for (int k = -R; k <= R; ++k) v[k + R] = __ldg(src + p + k);
+  const float* row = src + (p - i);
+  float w0 = __ldg(row), w1 = __ldg(row + 1);
+  float wn = __ldg(row + (n - 1)), wm = __ldg(row + (n - 2));
+  float slo = w0 - w1, shi = wn - wm;
+  float fi = (float)i, fr = (float)(n - 1 - i);
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    float e = (float)(R - k) - fi;  // ghost depth below node 0 (<= 0: a real node)
+    v[k] = (e > 0.f) ? fmaf(e, slo, w0) : v[k];
+  }
+#pragma unroll
+  for (int k = R + 1; k <= 2 * R; ++k) {
+    float e = (float)(k - R) - fr;  // ghost depth beyond node n-1
+    v[k] = (e > 0.f) ? fmaf(e, shi, wn) : v[k];
+  }
+}
+
 // ------------------------------------------------------------- slopes
 
 // Both one-sided WENO5 slopes (Jiang & Peng) at a node, from the six
@@ -329,8 +358,9 @@ struct Slopes<5> {
 };
 
 // L(src) at node p with multi-index idx; also returns src[p] in `center`.
-// The last axis is the fastest, so its stride is 1; its neighbours are then
-// immediate offsets of one address.
+// The last axis is the fastest (stride 1); its line is loaded branch-free at
+// immediate offsets (load_fast_line).  src needs at least 3 readable guard
+// floats before its first and after its last node.
 template <int D, int S, int M>
 __device__ __forceinline__ float lf_rhs(const DevGrid& g, const float* __restrict__ src, int p,
                                         const int (&idx)[D], const float (&x)[D], float& center) {
@@ -340,7 +370,10 @@ __device__ __forceinline__ float lf_rhs(const DevGrid& g, const float* __restric
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     float v[2 * R + 1];
-    load_line<R>(src, p, d == D - 1 ? 1 : g.stride[d], idx[d], g.n[d], v);
+    if (d == D - 1)
+      load_fast_line<R>(src, p, idx[d], g.n[d], v);
+    else
+      load_line<R>(src, p, g.stride[d], idx[d], g.n[d], v);
     if (d == D - 1) center = v[R];
     float pm, pp;
     Slopes<S>::eval(v, g, d, pm, pp);

@@ -29,6 +29,7 @@ struct hj_grid_s {
   float* A = nullptr;      // RK stage 1
   float* B = nullptr;      // RK stage 2
   float* snap = nullptr;   // W at the start of the current check window
+  float* raw[4] = {nullptr, nullptr, nullptr, nullptr};  // allocations behind W, A, B, snap
   float* tab = nullptr;    // per-index coefficient table of the model
   unsigned* dscal = nullptr;  // device scalars: [0..3] alpha bits, [4] residual bits, [5] flag
   unsigned* hscal = nullptr;  // pinned host mirror of dscal
@@ -51,6 +52,11 @@ struct hj_grid_s {
 };
 
 namespace hja {
+
+// Guard floats before the first and after the last node of every field.
+// The stencil loads the fastest-axis line unclamped, up to 3 nodes past
+// either end of the field.
+constexpr size_t kGuard = 64;
 
 hj_status fail(hj_status s, const char* fmt, ...);
 hjd::DevGrid devgrid(const hj_grid g);

@@ -5,7 +5,9 @@
 // another framework's pool).
 //
 // The scratch lives in one file-scope device array (below), shared by every
-// call and held by each GPU that loads the library until exit.  Host code
+// call and held by each GPU that loads the library until exit.  It holds the
+// coefficient accumulator, the model table, a guarded working copy of the
+// caller's W and the two Runge-Kutta stage fields.  Host code
 // never passes the symbol itself to a kernel: on the host that name is only
 // a stand-in, not a device address.  Instead, the first call on each device
 // asks the runtime for the array's device address with that device current,
@@ -21,8 +23,11 @@ namespace {
 
 constexpr size_t kHeadBytes = 256;                                    // alpha bits (4 x u32)
 constexpr size_t kTabBytes = sizeof(float) * HJ_STATIC_MAX_AXIS;      // g tan(th) table
-constexpr size_t kFieldBytes = sizeof(float) * (size_t)HJ_STATIC_MAX_POINTS;
-constexpr size_t kScratchBytes = kHeadBytes + kTabBytes + 2 * kFieldBytes;
+// one field: guard floats, HJ_STATIC_MAX_POINTS nodes, guard floats
+constexpr size_t kGuardBytes = sizeof(float) * hja::kGuard;
+constexpr size_t kFieldBytes = sizeof(float) * (size_t)HJ_STATIC_MAX_POINTS + 2 * kGuardBytes;
+// three fields: the working copy of W and the two Runge-Kutta stages
+constexpr size_t kScratchBytes = kHeadBytes + kTabBytes + 3 * kFieldBytes;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
 
@@ -158,9 +163,14 @@ extern "C" hj_status hj_solve_fixed_static(int ndim, const int* n, const double*
   if ((st = scratch_address(dev, &base)) != HJ_OK) return st;
   unsigned* alpha_bits = reinterpret_cast<unsigned*>(base);
   float* tab = reinterpret_cast<float*>(base + kHeadBytes);
-  float* A = reinterpret_cast<float*>(base + kHeadBytes + kTabBytes);
-  float* B = reinterpret_cast<float*>(base + kHeadBytes + kTabBytes + kFieldBytes);
+  unsigned char* fields = base + kHeadBytes + kTabBytes;
+  // the stencil reads a few floats past both ends of its source, so the
+  // solve runs on a guarded working copy of the caller's W
+  float* Wk = reinterpret_cast<float*>(fields + kGuardBytes);
+  float* A = reinterpret_cast<float*>(fields + kFieldBytes + kGuardBytes);
+  float* B = reinterpret_cast<float*>(fields + 2 * kFieldBytes + kGuardBytes);
   cudaStream_t s = (cudaStream_t)cuda_stream;
+  const size_t wbytes = (size_t)npts * sizeof(float);
 
   if (model == HJ_QUAD_X4) {
     float host_tab[HJ_STATIC_MAX_AXIS];
@@ -180,18 +190,20 @@ extern "C" hj_status hj_solve_fixed_static(int ndim, const int* n, const double*
   for (int i = 0; i < ndim; ++i) std::memcpy(&g.alpha[i], &host_bits[i], 4);
   double step = dt > 0.0 ? dt : hja::cfl_dt(&g, 0.5);
   d = hja::devgrid(&g);
-  HJ_CU(launch_static_init(d, W, mode == HJ_WARM ? 1 : 0, s));
+  if (mode == HJ_WARM) HJ_CU(cudaMemcpyAsync(Wk, W, wbytes, cudaMemcpyDeviceToDevice, s));
+  HJ_CU(launch_static_init(d, Wk, mode == HJ_WARM ? 1 : 0, s));
   if (step > 0.0) {
     float fdt = (float)step;
-    hjd::StageArgs a1{W, W, A, nullptr, nullptr, fdt, 0, clamp, 0.f};
-    hjd::StageArgs a2{A, W, B, nullptr, nullptr, fdt, 0, clamp, 0.f};
-    hjd::StageArgs a3{B, W, W, nullptr, nullptr, fdt, 0, clamp, 0.f};
+    hjd::StageArgs a1{Wk, Wk, A, nullptr, nullptr, fdt, 0, clamp, 0.f};
+    hjd::StageArgs a2{A, Wk, B, nullptr, nullptr, fdt, 0, clamp, 0.f};
+    hjd::StageArgs a3{B, Wk, Wk, nullptr, nullptr, fdt, 0, clamp, 0.f};
     for (long long k = 0; k < steps; ++k) {
       HJ_CU(hjk::launch_stage(d, scheme, 1, a1, s));
       HJ_CU(hjk::launch_stage(d, scheme, 2, a2, s));
       HJ_CU(hjk::launch_stage(d, scheme, 3, a3, s));
     }
   }
+  HJ_CU(cudaMemcpyAsync(W, Wk, wbytes, cudaMemcpyDeviceToDevice, s));
   HJ_CU(cudaStreamSynchronize(s));
   return HJ_OK;
 }
