@@ -394,6 +394,7 @@ def main():
                                                     "x41_b1.0_monotone_band_samples.txt"))
         scen = {"decomposed_update": scenarios.decomposed_update(),
                 "adaptive_grid": scenarios.adaptive_grid(reference=ref),
+                "local_wind_update": scenarios.local_wind_update(),
                 "serving": scenarios.serving(args.serve_requests)}
     if rank != 0:
         return

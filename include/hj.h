@@ -157,6 +157,24 @@ hj_status hj_set_constraint_ball(hj_grid g, const double* centre, double radius)
  * blocks, ndim for HJ_DRIFT. */
 hj_status hj_set_disturbance_bound(hj_grid g, const double* d_lo, const double* d_hi, int nd);
 
+/* State-dependent disturbance box (Sec. II-C).  The GP gives a
+ * delta-confidence interval D(x) at every state; this sets it node by node.
+ *   - d_lo and d_hi hold nd * npts floats each, input-major: input j's
+ *     field is [j * npts, (j + 1) * npts), with the nodes row-major as in
+ *     hj_get_value.
+ *   - on_device = 1: the pointers are device memory; 0: host memory.
+ *     Either way the data is copied.
+ *   - The field replaces the uniform box.  A later hj_set_disturbance_bound
+ *     replaces the field.
+ *   - Costs two extra reads per node and RK stage per disturbance input.
+ *   - Warm starts stay exact while every interval of the prior lies inside
+ *     the new one at every node.
+ * HJ_ERR_ARG on NULL pointers, a bad nd, or a node where d_lo > d_hi or a
+ * value is not finite.  After that last rejection no disturbance bound is in
+ * force: solves fail with HJ_ERR_STATE until one is set again. */
+hj_status hj_set_disturbance_field(hj_grid g, const float* d_lo, const float* d_hi, int nd,
+                                   int on_device);
+
 /* Iterate Eq. 2 to convergence.
  * Starting value:
  *   - HJ_COLD starts from l.

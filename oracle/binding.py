@@ -30,7 +30,8 @@ class _Problem(ctypes.Structure):
                 ("model", ctypes.c_int), ("params", ctypes.c_double * 8),
                 ("nd", ctypes.c_int), ("d_lo", ctypes.c_double * MAXIN),
                 ("d_hi", ctypes.c_double * MAXIN), ("con_kind", ctypes.c_int),
-                ("con_a", ctypes.c_double * MAXD), ("con_b", ctypes.c_double * MAXD)]
+                ("con_a", ctypes.c_double * MAXD), ("con_b", ctypes.c_double * MAXD),
+                ("dflo", ctypes.c_void_p), ("dfhi", ctypes.c_void_p)]
 
 
 class _Opts(ctypes.Structure):
@@ -93,8 +94,14 @@ def _dp(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-def _problem(spec) -> _Problem:
+def _problem(spec, dfield=None) -> _Problem:
+    """ctypes problem for a spec; dfield = (d_lo, d_hi) arrays of shape
+    (nd,) + grid shape for a state-dependent disturbance box (kept alive by
+    the caller for the duration of the call)."""
     p = _Problem()
+    if dfield is not None:
+        p.dflo = dfield[0].ctypes.data
+        p.dfhi = dfield[1].ctypes.data
     p.ndim = spec.ndim
     for i in range(spec.ndim):
         p.n[i] = spec.n[i]
@@ -126,8 +133,11 @@ def set_num_threads(k: int) -> None:
 def solve(spec, scheme: int = 5, cfl: float = 0.5, dt: float = 0.0, tol: float = 1e-4,
           check_dt: float = 0.1, max_steps: int = 0, fixed_steps: int = 0,
           clamp: int = 0, warm: Optional[np.ndarray] = None,
-          band: float = 0.0, band_margin: int = 0) -> Tuple[np.ndarray, Dict]:
-    """Run the oracle solve; returns (W on the grid, stats)."""
+          band: float = 0.0, band_margin: int = 0,
+          dfield: Optional[Tuple[np.ndarray, np.ndarray]] = None) -> Tuple[np.ndarray, Dict]:
+    """Run the oracle solve; returns (W on the grid, stats).  dfield: optional
+    state-dependent disturbance box (d_lo, d_hi), each (nd,) + grid shape."""
+    dfield = _field(dfield)
     W = np.zeros(spec.n, dtype=np.float64)
     if warm is not None:
         W[...] = warm
@@ -135,7 +145,7 @@ def solve(spec, scheme: int = 5, cfl: float = 0.5, dt: float = 0.0, tol: float =
               fixed_steps=fixed_steps, clamp=clamp, warm=1 if warm is not None else 0,
               band=band, band_margin=band_margin)
     st = _Stats()
-    pr = _problem(spec)
+    pr = _problem(spec, dfield)
     rc = lib().or_solve(ctypes.byref(pr), ctypes.byref(o), _dp(W), ctypes.byref(st))
     if rc < 0:
         raise ValueError("oracle rejected the problem")
@@ -143,15 +153,23 @@ def solve(spec, scheme: int = 5, cfl: float = 0.5, dt: float = 0.0, tol: float =
                    converged=bool(st.converged), windows=st.windows, rc=rc)
 
 
-def alpha(spec) -> np.ndarray:
+def _field(dfield):
+    if dfield is None:
+        return None
+    return (np.ascontiguousarray(dfield[0], dtype=np.float64),
+            np.ascontiguousarray(dfield[1], dtype=np.float64))
+
+
+def alpha(spec, dfield=None) -> np.ndarray:
     a = np.zeros(spec.ndim)
-    pr = _problem(spec)
+    dfield = _field(dfield)
+    pr = _problem(spec, dfield)
     lib().or_alpha(ctypes.byref(pr), _dp(a))
     return a
 
 
-def cfl_dt(spec, cfl: float = 0.5) -> float:
-    a = alpha(spec)
+def cfl_dt(spec, cfl: float = 0.5, dfield=None) -> float:
+    a = alpha(spec, dfield)
     pr = _problem(spec)
     return lib().or_cfl_dt(ctypes.byref(pr), cfl, _dp(a))
 

@@ -83,6 +83,8 @@ typedef struct {
   int con_kind;
   double con_a[OR_MAXD];  /* box lo, or ball centre                              */
   double con_b[OR_MAXD];  /* box hi, or ball radius in con_b[0]                  */
+  const double* dflo;     /* state-dependent disturbance box (Sec. II-C): input  */
+  const double* dfhi;     /* j's bound at node k is [j * npts + k]; NULL = box   */
 } or_problem;
 
 typedef struct {
@@ -209,8 +211,21 @@ static void box_vertex(int m, const double* lo, const double* hi, int k, double*
   for (int i = 0; i < m; ++i) v[i] = ((k >> i) & 1) ? hi[i] : lo[i];
 }
 
-/* H(x, p) = max_u min_d p . f(x, u, d), by enumeration of input-box vertices */
-double or_hamiltonian(const or_problem* P, const double* x, const double* p) {
+/* Disturbance box at node pt: the state-dependent field when set, else the
+ * uniform box. */
+static void dist_box(const or_problem* P, long pt, double* lo, double* hi) {
+  long npts = 1;
+  for (int d = 0; d < P->ndim; ++d) npts *= P->n[d];
+  for (int j = 0; j < P->nd; ++j) {
+    lo[j] = P->dflo ? P->dflo[j * npts + pt] : P->d_lo[j];
+    hi[j] = P->dfhi ? P->dfhi[j * npts + pt] : P->d_hi[j];
+  }
+}
+
+/* H(x, p) = max_u min_d p . f(x, u, d) over the input boxes' vertices, with
+ * the disturbance box (dlo, dhi) */
+static double hamiltonian_box(const or_problem* P, const double* x, const double* p,
+                              const double* dlo, const double* dhi) {
   double ulo[OR_MAXIN] = {0}, uhi[OR_MAXIN] = {0}, u[OR_MAXIN] = {0}, dd[OR_MAXIN] = {0};
   double f[OR_MAXD];
   int nu = model_nu(P);
@@ -220,7 +235,7 @@ double or_hamiltonian(const or_problem* P, const double* x, const double* p) {
     box_vertex(nu, ulo, uhi, ku, u);
     double worst = INFINITY;
     for (int kd = 0; kd < (1 << P->nd); ++kd) {
-      box_vertex(P->nd, P->d_lo, P->d_hi, kd, dd);
+      box_vertex(P->nd, dlo, dhi, kd, dd);
       model_f(P, x, u, dd, f);
       double s = 0.0;
       for (int i = 0; i < P->ndim; ++i) s += p[i] * f[i];
@@ -229,6 +244,12 @@ double or_hamiltonian(const or_problem* P, const double* x, const double* p) {
     if (worst > best) best = worst;
   }
   return best;
+}
+
+/* H(x, p) = max_u min_d p . f(x, u, d), by enumeration of input-box vertices,
+ * with the uniform disturbance box */
+double or_hamiltonian(const or_problem* P, const double* x, const double* p) {
+  return hamiltonian_box(P, x, p, P->d_lo, P->d_hi);
 }
 
 /* a_i = max over grid nodes and input vertices of |f_i(x, u, d)| */
@@ -241,12 +262,14 @@ void or_alpha(const or_problem* P, double* alpha) {
   for (long pt = 0; pt < npts; ++pt) {
     long idx[OR_MAXD];
     double x[OR_MAXD], f[OR_MAXD], u[OR_MAXIN] = {0}, dd[OR_MAXIN] = {0};
+    double dlo[OR_MAXIN], dhi[OR_MAXIN];
     grid_unravel(P, pt, idx);
     grid_coords(P, idx, x);
+    dist_box(P, pt, dlo, dhi);
     for (int ku = 0; ku < (1 << nu); ++ku) {
       box_vertex(nu, ulo, uhi, ku, u);
       for (int kd = 0; kd < (1 << P->nd); ++kd) {
-        box_vertex(P->nd, P->d_lo, P->d_hi, kd, dd);
+        box_vertex(P->nd, dlo, dhi, kd, dd);
         model_f(P, x, u, dd, f);
         for (int i = 0; i < P->ndim; ++i)
           if (fabs(f[i]) > alpha[i]) alpha[i] = fabs(f[i]);
@@ -367,7 +390,9 @@ static void lf_rhs(const or_problem* P, int scheme, const double* alpha,
       else first_order(v, h, &pm[d], &pp[d]);
       pbar[d] = 0.5 * (pm[d] + pp[d]);
     }
-    double L = or_hamiltonian(P, x, pbar);
+    double dlo[OR_MAXIN], dhi[OR_MAXIN];
+    dist_box(P, pt, dlo, dhi);
+    double L = hamiltonian_box(P, x, pbar, dlo, dhi);
     for (int d = 0; d < P->ndim; ++d) L += alpha[d] * 0.5 * (pp[d] - pm[d]);
     out[pt] = L;
   }

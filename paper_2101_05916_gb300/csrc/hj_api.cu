@@ -87,6 +87,10 @@ hjd::DevGrid devgrid(const hj_grid g) {
   }
   for (int i = 0; i < HJ_MAX_DIM; ++i) d.alpha[i] = g->alpha[i];
   d.tab = g->tab;
+  if (g->dfield_nd > 0) {
+    d.dflo = g->dfield;
+    d.dfhi = g->dfield + (size_t)g->dfield_nd * (size_t)g->npts;
+  }
   return d;
 }
 
@@ -326,6 +330,7 @@ void hj_grid_destroy(hj_grid g) {
     drop_graph(g);
     for (int i = 0; i < 4; ++i) cudaFree(g->raw[i]);
     cudaFree(g->tab);
+    cudaFree(g->dfield);
     cudaFree(g->dscal);
     cudaFree(g->qbuf);
     if (g->hscal) cudaFreeHost(g->hscal);
@@ -485,6 +490,44 @@ hj_status hj_set_disturbance_bound(hj_grid g, const double* d_lo, const double* 
     g->d_lo[i] = i < nd ? d_lo[i] : 0.0;
     g->d_hi[i] = i < nd ? d_hi[i] : 0.0;
   }
+  g->dfield_nd = 0;  // a uniform box replaces any field
+  invalidate(g);
+  return HJ_OK;
+}
+
+hj_status hj_set_disturbance_field(hj_grid g, const float* d_lo, const float* d_hi, int nd,
+                                   int on_device) {
+  if (!g || !d_lo || !d_hi) return fail(HJ_ERR_ARG, "NULL argument");
+  if (nd < 1 || nd > HJ_MAX_DIM) return fail(HJ_ERR_ARG, "bad number of disturbance inputs");
+  DeviceGuard dg(g->device);
+  size_t n = (size_t)nd * (size_t)g->npts;
+  if (!g->dfield || g->dfield_nd != nd) {
+    cudaFree(g->dfield);
+    g->dfield = nullptr;
+    g->dfield_nd = 0;
+    HJ_CU(cudaMalloc(&g->dfield, 2 * n * sizeof(float)));
+  }
+  cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  HJ_CU(cudaMemcpyAsync(g->dfield, d_lo, n * sizeof(float), k, g->stream));
+  HJ_CU(cudaMemcpyAsync(g->dfield + n, d_hi, n * sizeof(float), k, g->stream));
+  HJ_CU(cudaMemsetAsync(g->dscal + 5, 0, sizeof(unsigned), g->stream));
+  HJ_CU(hjk::launch_field_check(g->dfield, g->dfield + n, (long long)n, (int*)(g->dscal + 5),
+                                g->stream));
+  HJ_CU(cudaMemcpyAsync(g->hscal + 5, g->dscal + 5, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                        g->stream));
+  HJ_CU(cudaStreamSynchronize(g->stream));
+  if (g->hscal[5]) {
+    // the rejected values are gone with the buffer; no bound is in force now
+    cudaFree(g->dfield);
+    g->dfield = nullptr;
+    g->dfield_nd = 0;
+    g->nd = 0;
+    invalidate(g);
+    return fail(HJ_ERR_ARG, "disturbance field: need finite d_lo <= d_hi at every node");
+  }
+  g->dfield_nd = nd;
+  g->nd = nd;
+  for (int i = 0; i < HJ_MAX_DIM; ++i) g->d_lo[i] = g->d_hi[i] = 0.0;
   invalidate(g);
   return HJ_OK;
 }

@@ -52,6 +52,8 @@ struct DevGrid {
   float ca[MAXD], cb[MAXD];
   float alpha[MAXD];   // Lax-Friedrichs coefficients
   const float* tab;    // quad_x4: g * tan(th_j) per th index
+  const float* dflo;   // state-dependent disturbance box, input-major nd x npts
+  const float* dfhi;   // (nullptr: the uniform box dlo/dhi)
 };
 
 // Arguments of one Runge-Kutta stage launch.
@@ -114,15 +116,29 @@ __device__ __forceinline__ float margin(const DevGrid& g, const float (&x)[D]) {
 // ------------------------------------------------------------- dynamics
 
 // H(x, p) = max_u min_d p . f(x, u, d) in closed (bang-bang) form.
+// Disturbance interval of input j at node `node`: the state-dependent field
+// when one is set (a GP confidence band, Sec. II-C), else the uniform box.
+__device__ __forceinline__ void dist_box(const DevGrid& g, int j, int node, float& lo, float& hi) {
+  if (g.dflo) {
+    lo = __ldg(g.dflo + (size_t)j * g.npts + node);
+    hi = __ldg(g.dfhi + (size_t)j * g.npts + node);
+  } else {
+    lo = g.dlo[j];
+    hi = g.dhi[j];
+  }
+}
+
 template <int M, int D>
 __device__ __forceinline__ float hamiltonian(const DevGrid& g, const float (&x)[D],
-                                             const int (&idx)[D], const float (&p)[D]) {
+                                             const int (&idx)[D], const float (&p)[D], int node) {
   if constexpr (M == M_QUAD_Z) {
     // f = (vz, kT u - g + d); prm = (kT, g, u_lo, u_hi)
     float a = p[1] * g.prm[0];
     float H = fmaf(p[0], x[1], -p[1] * g.prm[1]);
     H += fmaxf(a * g.prm[2], a * g.prm[3]);
-    H += fminf(p[1] * g.dlo[0], p[1] * g.dhi[0]);
+    float dl, dh;
+    dist_box(g, 0, node, dl, dh);
+    H += fminf(p[1] * dl, p[1] * dh);
     return H;
   } else if constexpr (M == M_QUAD_X4) {
     // f = (v, g tan th, -d1 th + w, -d0 th + n0 u) + d e_axis
@@ -135,13 +151,19 @@ __device__ __forceinline__ float hamiltonian(const DevGrid& g, const float (&x)[
     H = fmaf(-p[3] * g.prm[2], x[2], H);
     H += fmaxf(a * g.prm[4], a * g.prm[5]);
     float pa = (g.prm[6] != 0.f) ? p[1] : p[0];
-    H += fminf(pa * g.dlo[0], pa * g.dhi[0]);
+    float dl, dh;
+    dist_box(g, 0, node, dl, dh);
+    H += fminf(pa * dl, pa * dh);
     return H;
   } else {
     // drift: f = d, one interval per axis
     float H = 0.f;
 #pragma unroll
-    for (int d = 0; d < D; ++d) H += fminf(p[d] * g.dlo[d], p[d] * g.dhi[d]);
+    for (int d = 0; d < D; ++d) {
+      float dl, dh;
+      dist_box(g, d, node, dl, dh);
+      H += fminf(p[d] * dl, p[d] * dh);
+    }
     return H;
   }
 }
@@ -149,20 +171,23 @@ __device__ __forceinline__ float hamiltonian(const DevGrid& g, const float (&x)[
 // Per-axis max over the input box vertices of |f_i(x, u, d)| at one node.
 template <int M, int D>
 __device__ __forceinline__ void abs_f_max(const DevGrid& g, const float (&x)[D],
-                                          const int (&idx)[D], float (&m)[D]) {
+                                          const int (&idx)[D], float (&m)[D], int node) {
   if constexpr (M == M_QUAD_Z) {
     m[0] = fmaxf(m[0], fabsf(x[1]));
     float kT = g.prm[0], gg = g.prm[1];
+    float dl, dh;
+    dist_box(g, 0, node, dl, dh);
     float e = 0.f;
-    e = fmaxf(e, fabsf(kT * g.prm[2] - gg + g.dlo[0]));
-    e = fmaxf(e, fabsf(kT * g.prm[2] - gg + g.dhi[0]));
-    e = fmaxf(e, fabsf(kT * g.prm[3] - gg + g.dlo[0]));
-    e = fmaxf(e, fabsf(kT * g.prm[3] - gg + g.dhi[0]));
+    e = fmaxf(e, fabsf(kT * g.prm[2] - gg + dl));
+    e = fmaxf(e, fabsf(kT * g.prm[2] - gg + dh));
+    e = fmaxf(e, fabsf(kT * g.prm[3] - gg + dl));
+    e = fmaxf(e, fabsf(kT * g.prm[3] - gg + dh));
     m[1] = fmaxf(m[1], e);
   } else if constexpr (M == M_QUAD_X4) {
     float gt = __ldg(g.tab + idx[2]);
     bool ax1 = g.prm[6] != 0.f;
-    float dl = g.dlo[0], dh = g.dhi[0];
+    float dl, dh;
+    dist_box(g, 0, node, dl, dh);
     float f0 = ax1 ? fabsf(x[1]) : fmaxf(fabsf(x[1] + dl), fabsf(x[1] + dh));
     float f1 = ax1 ? fmaxf(fabsf(gt + dl), fabsf(gt + dh)) : fabsf(gt);
     float f2 = fabsf(fmaf(-g.prm[1], x[2], x[3]));
@@ -174,7 +199,11 @@ __device__ __forceinline__ void abs_f_max(const DevGrid& g, const float (&x)[D],
     m[3] = fmaxf(m[3], f3);
   } else {
 #pragma unroll
-    for (int d = 0; d < D; ++d) m[d] = fmaxf(m[d], fmaxf(fabsf(g.dlo[d]), fabsf(g.dhi[d])));
+    for (int d = 0; d < D; ++d) {
+      float dl, dh;
+      dist_box(g, d, node, dl, dh);
+      m[d] = fmaxf(m[d], fmaxf(fabsf(dl), fabsf(dh)));
+    }
   }
 }
 
@@ -380,7 +409,7 @@ __device__ __forceinline__ float lf_rhs(const DevGrid& g, const float* __restric
     pbar[d] = Slopes<S>::half(g, d) * (pm + pp);
     diss = fmaf(Slopes<S>::half_alpha(g, d), pp - pm, diss);
   }
-  return hamiltonian<M, D>(g, x, idx, pbar) + diss;
+  return hamiltonian<M, D>(g, x, idx, pbar, p) + diss;
 }
 
 // Maximum of non-negative float bit patterns across the block, then one

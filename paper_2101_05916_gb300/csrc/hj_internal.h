@@ -34,6 +34,10 @@ cudaError_t launch_prolong(const hjd::DevGrid& c, const float* Wc, const hjd::De
 cudaError_t launch_query(const hjd::DevGrid& g, const float* W, int npts, const double* x,
                          double* out, int* bad, int grad, cudaStream_t s);
 
+// *bad = 1 when some of the n pairs (lo[k], hi[k]) has lo > hi or a non-finite value.
+cudaError_t launch_field_check(const float* lo, const float* hi, long long n, int* bad,
+                               cudaStream_t s);
+
 // Whether (model, ndim, scheme) has a compiled stencil.
 bool stage_supported(int model, int ndim, int scheme);
 

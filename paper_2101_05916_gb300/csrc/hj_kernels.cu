@@ -62,7 +62,7 @@ __global__ void alpha_kernel(const DevGrid g, unsigned* out) {
     float x[D];
     unravel<D>(g, pt, idx);
     coords<D>(g, idx, x);
-    hjd::abs_f_max<M, D>(g, x, idx, m);
+    hjd::abs_f_max<M, D>(g, x, idx, m, pt);
   }
 #pragma unroll
   for (int d = 0; d < D; ++d) {
@@ -300,6 +300,27 @@ cudaError_t launch_prolong(const DevGrid& c, const float* Wc, const DevGrid& f, 
     case 4: prolong_kernel<4><<<nb, 256, 0, s>>>(c, Wc, f, Wf, bad); break;
     default: return cudaErrorInvalidValue;
   }
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+// *bad = 1 when some lo[k] > hi[k] or either is not finite.
+__global__ void field_check_kernel(const float* __restrict__ lo, const float* __restrict__ hi,
+                                   long long n, int* bad) {
+  int found = 0;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    float a = lo[k], b = hi[k];
+    found |= !(isfinite(a) && isfinite(b) && a <= b);
+  }
+  if (__syncthreads_or(found) && threadIdx.x == 0) *bad = 1;
+}
+
+cudaError_t launch_field_check(const float* lo, const float* hi, long long n, int* bad,
+                               cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  unsigned nb = (unsigned)std::min<long long>((n + 255) / 256, 152 * 16);
+  field_check_kernel<<<nb, 256, 0, s>>>(lo, hi, n, bad);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }

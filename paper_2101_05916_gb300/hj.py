@@ -92,6 +92,7 @@ SIGNATURES = {
     "hj_set_constraint": (_i, [_vp, _P(_d), _P(_d)]),
     "hj_set_constraint_ball": (_i, [_vp, _P(_d), _d]),
     "hj_set_disturbance_bound": (_i, [_vp, _P(_d), _P(_d), _i]),
+    "hj_set_disturbance_field": (_i, [_vp, _vp, _vp, _i, _i]),
     "hj_solve": (_i, [_vp, _i, _P(hj_solve_opts), _P(hj_solve_stats)]),
     "hj_solve_batch": (_i, [_P(_vp), _i, _P(_i), _P(hj_solve_opts), _i, _P(hj_solve_stats),
                             _P(_i)]),
@@ -205,6 +206,27 @@ def hj_set_constraint_ball(g: int, centre: Sequence[float], radius: float) -> No
 
 def hj_set_disturbance_bound(g: int, d_lo: Sequence[float], d_hi: Sequence[float]) -> None:
     _check(lib().hj_set_disturbance_bound(g, _darr(d_lo), _darr(d_hi), len(d_lo)))
+
+
+def hj_set_disturbance_field(g: int, d_lo, d_hi) -> None:
+    """State-dependent disturbance box: d_lo, d_hi of shape (nd,) + grid shape
+    (numpy, host) or flat float32 CUDA tensors of nd * npts values."""
+    try:
+        import torch
+        if isinstance(d_lo, torch.Tensor):
+            npts = lib().hj_grid_points(g)
+            nd = d_lo.numel() // npts
+            _check(lib().hj_set_disturbance_field(g, d_lo.data_ptr(), d_hi.data_ptr(), nd, 1))
+            return
+    except ImportError:  # pragma: no cover
+        pass
+    lo = np.ascontiguousarray(d_lo, dtype=np.float32)
+    hi = np.ascontiguousarray(d_hi, dtype=np.float32)
+    npts = lib().hj_grid_points(g)
+    nd = lo.size // npts
+    if lo.size != nd * npts or hi.size != lo.size:
+        raise ValueError("field must hold nd * npts values")
+    _check(lib().hj_set_disturbance_field(g, lo.ctypes.data, hi.ctypes.data, nd, 0))
 
 
 def make_opts(scheme: int = HJ_WENO5, cfl: float = 0.5, dt: float = 0.0, tol: float = 1e-4,
@@ -456,6 +478,9 @@ class Grid:
 
     def set_disturbance_bound(self, d_lo, d_hi) -> None:
         hj_set_disturbance_bound(self.handle, d_lo, d_hi)
+
+    def set_disturbance_field(self, d_lo, d_hi) -> None:
+        hj_set_disturbance_field(self.handle, d_lo, d_hi)
 
     def solve(self, mode: int = HJ_COLD, **kw) -> Dict:
         rc, st = hj_solve(self.handle, mode, make_opts(**kw))

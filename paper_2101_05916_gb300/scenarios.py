@@ -9,6 +9,8 @@ solving, through the same C ABI:
   The plain way is three cold single-grid solves, one after another.
 * adaptive_grid (Sec. III-C): a coarse cold solve, migration to the fine
   grid, and a warm fine solve.  The plain way is a cold fine solve.
+* local_wind_update (Sec. II-C, III-B): the wind bound rises near one
+  place only; warm start from the previous result against a cold solve.
 * serving: a seeded request trace replayed through the continuous-batching
   server.  The plain way is one cold single-grid solve per request, in
   arrival order.
@@ -177,6 +179,57 @@ def adaptive_grid(nc: int = 31, nf: int = 81, b: float = 1.0,
                 mean_abs=float(np.abs(v - ref).mean()),
                 sign_agreement=float(np.mean((v >= 0) == (ref >= 0))))
     return out
+
+
+def local_wind_update(n4: int = 61, n2: int = 201, base: float = 0.5,
+                      bumps: Sequence[tuple] = ((0.5, 3.0, 0.6), (0.5, -2.5, 0.6),
+                                                (0.8, 3.2, 0.4))) -> Dict:
+    """State-dependent wind (Sec. II-C, V-A): the GP learns that the wind is
+    stronger near one place, so the bound rises locally.  Each bump
+    (height, centre on the position axis, width) is added to the previous
+    field, so the previous fixed point dominates the new one and the warm
+    start stays exact (Sec. III-B).  Every update of the x (n4^4) and z
+    (n2^2) subsystems is solved warm from the previous result and cold."""
+    specs = [wl.quad_x4(n4, base), wl.quad_z(n2, base)]
+    rows = []
+    for spec in specs:
+        opts = hj.make_opts(**_opts_for(spec))
+        g = hj.Grid.from_spec(spec)
+        lo, hi = wl.wind_field(spec, base, 0.0, 0, 0.0, 1.0)
+        g.set_disturbance_field(lo, hi)
+        rc, st = hj.hj_solve(g.handle, hj.HJ_COLD, opts, raise_on_error=False)
+        for height, centre, width in bumps:
+            # the z axis spans [0, 3]: put its bumps at the same relative place
+            c = centre if spec.ndim == 4 else 1.5 + 0.3 * centre
+            w = width if spec.ndim == 4 else 0.3 * width
+            dlo, dhi = wl.wind_field(spec, 0.0, height, 0, c, w)
+            lo, hi = lo + dlo, hi + dhi
+            g.set_disturbance_field(lo, hi)
+            _sync()
+            t0 = time.perf_counter()
+            rcw, stw = hj.hj_solve(g.handle, hj.HJ_WARM, opts, raise_on_error=False)
+            _sync()
+            t1 = time.perf_counter()
+            Ww = g.value()
+            gc = hj.Grid.from_spec(spec)
+            gc.set_disturbance_field(lo, hi)
+            _sync()
+            t2 = time.perf_counter()
+            rcc, stc = hj.hj_solve(gc.handle, hj.HJ_COLD, opts, raise_on_error=False)
+            _sync()
+            t3 = time.perf_counter()
+            Wc = gc.value()
+            gc.close()
+            rows.append(dict(grid=spec.name + "%s" % (spec.n,), bump=(height, c, w),
+                             warm_ms=1e3 * (t1 - t0), warm_steps=stw["steps"],
+                             cold_ms=1e3 * (t3 - t2), cold_steps=stc["steps"],
+                             statuses=[int(rcw), int(rcc)],
+                             sign_agreement=float(np.mean((Ww >= 0) == (Wc >= 0))),
+                             max_abs_diff_in_band=float(
+                                 np.abs(Ww - Wc)[np.abs(Wc) <= 0.5].max())))
+        g.close()
+    speed = [r["cold_ms"] / r["warm_ms"] for r in rows]
+    return dict(base=base, updates=rows, warm_speedup_p50=float(np.percentile(speed, 50)))
 
 
 def load_reference(path: str) -> Optional[Dict]:

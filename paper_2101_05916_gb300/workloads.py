@@ -178,6 +178,19 @@ def serving_trace(count: int = 256, rate_hz: float = 20.0, seed: int = 20210115,
     return out
 
 
+def wind_field(spec: ProblemSpec, base: float, bump: float, axis: int, centre: float,
+               width: float) -> Tuple[np.ndarray, np.ndarray]:
+    """A GP-like state-dependent wind interval (Sec. II-C, Sec. V-A: the fan's
+    wind is strongest near one place and fades away from it):
+    |d| <= base + bump * exp(-((x_axis - centre) / width)^2) at every node.
+    Returns (d_lo, d_hi), each of shape (nd,) + grid shape."""
+    xs = np.meshgrid(*spec.coords(), indexing="ij")[axis]
+    b = base + bump * np.exp(-((xs - centre) / width) ** 2)
+    nd = len(spec.d_lo)
+    hi = np.broadcast_to(b, (nd,) + tuple(spec.n)).astype(np.float64).copy()
+    return -hi, hi
+
+
 def seeded_field(spec: ProblemSpec, seed: int, scale: float = 1.0) -> np.ndarray:
     """A reproducible random field on the grid (for layout and edge tests)."""
     rng = np.random.Generator(np.random.PCG64(seed))

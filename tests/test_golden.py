@@ -22,7 +22,7 @@ def _load(name):
 
 def test_oracle_matches_stored_z41():
     s = wl.quad_z(41, 0.5)
-    W, st = oracle.solve(s, scheme=2, tol=1e-9)
+    W, st = oracle.solve(s, scheme=2, tol=1e-9, max_steps=50000)
     ref = _load("z41_eno2_b0.5_converged.txt").reshape(s.n)
     assert np.abs(W - ref).max() < 1e-12
 
