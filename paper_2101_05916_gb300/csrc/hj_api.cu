@@ -62,14 +62,11 @@ hjd::DevGrid devgrid(const hj_grid g) {
     d.lo_d[i] = g->lo[i];
     d.h_d[i] = g->h[i];
     d.ih[i] = (float)(1.0 / g->h[i]);
-    d.ih6[i] = (float)(1.0 / (6.0 * g->h[i]));
     // WENO epsilon floor: 1e-18 in divided differences, on undivided ones
-    // times h^2, times the 12/13 scale of the smoothness indicators
-    d.wfloor[i] = (float)(12.0 / 13.0 * 1e-18 * g->h[i] * g->h[i]);
+    // times h^2, times the 3/4 scale of the smoothness indicators
+    d.wfloor[i] = (float)(0.75 * 1e-18 * g->h[i] * g->h[i]);
     d.hih[i] = (float)(0.5 / g->h[i]);
-    d.hih6[i] = (float)(0.5 / (6.0 * g->h[i]));
     d.haih[i] = (float)(0.5 * (double)g->alpha[i] / g->h[i]);
-    d.haih6[i] = (float)(0.5 * (double)g->alpha[i] / (6.0 * g->h[i]));
   }
   d.model = g->model;
   for (int i = 0; i < 8; ++i) d.prm[i] = (float)g->params[i];

@@ -38,12 +38,9 @@ struct DevGrid {
   double lo_d[MAXD];   // the same box in double, for interpolation
   double h_d[MAXD];
   float ih[MAXD];      // 1 / h
-  float ih6[MAXD];     // 1 / (6 h), folds the 1/6 of the WENO candidates
-  float hih[MAXD];     // 0.5 / h        (first order, ENO2)
-  float hih6[MAXD];    // 0.5 / (6 h)    (WENO5)
+  float hih[MAXD];     // 0.5 / h
   float haih[MAXD];    // 0.5 a / h
-  float haih6[MAXD];   // 0.5 a / (6 h)
-  float wfloor[MAXD];  // WENO epsilon floor on undivided differences: 1e-18 h^2
+  float wfloor[MAXD];  // WENO epsilon floor on undivided differences: 1e-18 h^2, times 3/4
   int model;
   float prm[8];
   float dlo[MAXD], dhi[MAXD];
@@ -272,69 +269,80 @@ __device__ __forceinline__ void load_fast_line(const float* __restrict__ src, in
 
 // ------------------------------------------------------------- slopes
 
+// Packed FP32 pairs (Blackwell FFMA2 / FMUL2 / FADD2): one instruction
+// issues the same operation on both lanes, each lane rounded exactly like
+// the scalar fmaf / mul / add.
+__device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
 // Both one-sided WENO5 slopes (Jiang & Peng) at a node, from the six
 // undivided differences D_k = v[k+1] - v[k] of the line values v at offsets
 // -3..3.  The left-biased slope uses D0..D4; the right-biased slope uses
-// D5..D1 in upwind order.  Returns 6 h p- and 6 h p+; the caller folds in
-// 1 / (6 h).
+// D5..D1 in upwind order.  Returns h p- and h p+; the caller folds in 1 / h.
 //
-// The arithmetic is the textbook scheme, rearranged to save instructions:
-//   - Second differences t and the max |D| are shared by the two sides.
-//   - Each smoothness indicator 13/12 t^2 + 1/4 u^2 is computed as
-//     t^2 + (3/13) u^2, i.e. scaled by 12/13.  The epsilon is scaled by the
-//     same factor, so every S_k + eps changes by one common factor, which
-//     normalised weights cancel.
+// The right-biased slope is the left-biased formula applied to the mirrored
+// differences, so both run as the two lanes of packed FP32 pairs: lane x
+// holds the left side's operand, lane y the right side's.  Packed pairs
+// halve the issue slots of the arithmetic.
+//
+// The arithmetic is the textbook scheme, rewritten in the second
+// differences A, B, C, E of the five upwind differences X0..X4 (A = X1 - X0,
+// B = X2 - X1, C = X3 - X2, E = X4 - X3) to save operations:
+//   - Smoothness indicators.  13/12 t^2 + 1/4 u^2 of each candidate equals
+//     4/3 of a sum of two squares:
+//       S1 = (A - 11/8 B)^2 + 39/64 B^2,
+//       S2 = (B - 5/8 C)^2 + 39/64 C^2,
+//       S3 = (E - 11/8 C)^2 + 39/64 C^2.
+//     The epsilon gets the same factor 3/4, so every S_k + eps scales by
+//     one common factor, which normalised weights cancel.  No term can
+//     cancel another.
 //   - Nonlinear weights a_k = c_k / (S_k + eps)^2 are evaluated as
 //     c_1 s_2^2 s_3^2, c_2 s_1^2 s_3^2, c_3 s_1^2 s_2^2 with
-//     s_k = S_k / eps + 1.  That is the same normalised set, multiplied
-//     through by a common factor.  Since S_k <= 34 max D^2 and
-//     eps >= 1e-6 max D^2, every s_k lies in [1, 3.4e7], so the products
-//     stay inside FP32 range.  It takes one reciprocal per weight set.
-//   - The linear weights (1/10, 6/10, 3/10) are folded into the candidate
-//     coefficients.
+//     s_k = S_k / eps + 1: the same normalised set, multiplied through by a
+//     common factor.  Since S_k <= 34 max D^2 and eps >= 1e-6 max D^2, every
+//     s_k lies in [1, 3.4e7], so the products stay inside FP32 range.
+//   - Candidates.  The three third-order candidates times their linear
+//     weights (1/10, 6/10, 3/10) sum to X2 times the weight sum plus
+//     (B - 2A/5)/2, (B/2 + C) 6/5 and (C - E/4) 6/5 times the weights.  With
+//     s_1^2 scaled by 12/5, the slope is X2 + N / M where
+//       N = Q1 (B - 2A/5) + Q2 (B/2 + C) + Q3 (C - E/4),
+//       M = 6/5 Q1 + 3 Q2 + 3/2 Q3,
+//       Q1 = s_2^2 s_3^2, Q2 = 12/5 s_1^2 s_3^2, Q3 = 12/5 s_1^2 s_2^2.
+//     It takes one reciprocal per side.
 __device__ __forceinline__ void weno5_pair(float D0, float D1, float D2, float D3, float D4,
-                                           float D5, float floor_, float& pm6h, float& pp6h) {
-  const float k = 0.48038446141526137f;  // sqrt(3/13)
-  // second differences of the four difference triples
-  float t0 = fmaf(-2.f, D1, D0 + D2);
-  float t1 = fmaf(-2.f, D2, D1 + D3);
-  float t2 = fmaf(-2.f, D3, D2 + D4);
-  float t3 = fmaf(-2.f, D4, D3 + D5);
-  // sqrt(3/13)-scaled first-difference combinations of each role
-  float uA0 = fmaf(3.f * k, D2, fmaf(-4.f * k, D1, k * D0));   // (D0,D1,D2), left end
-  float uB1 = fmaf(k, D1, -k * D3);                            // (D1,D2,D3), centre
-  float uC2 = fmaf(3.f * k, D2, fmaf(-4.f * k, D3, k * D4));   // (D2,D3,D4), right end
-  float uC3 = fmaf(3.f * k, D3, fmaf(-4.f * k, D4, k * D5));   // (D3,D4,D5), right end
-  float uB2 = fmaf(k, D2, -k * D4);                            // (D2,D3,D4), centre
-  float uA1 = fmaf(3.f * k, D3, fmaf(-4.f * k, D2, k * D1));   // (D1,D2,D3), left end
-  // smoothness indicators (scaled by 12/13)
-  float Sm1 = fmaf(t0, t0, uA0 * uA0), Sm2 = fmaf(t1, t1, uB1 * uB1), Sm3 = fmaf(t2, t2, uC2 * uC2);
-  float Sp1 = fmaf(t3, t3, uC3 * uC3), Sp2 = fmaf(t2, t2, uB2 * uB2), Sp3 = fmaf(t1, t1, uA1 * uA1);
-  // epsilon = 1e-6 max D^2 + floor, scaled by 12/13 like the indicators
+                                           float D5, float floor_, float& pm_h, float& pp_h) {
+  const float2 A = make_float2(D1 - D0, D4 - D5), B = make_float2(D2 - D1, D3 - D4);
+  const float2 C = make_float2(D3 - D2, D2 - D3), E = make_float2(D4 - D3, D1 - D2);
+  const float2 X2 = make_float2(D2, D3);
+  const float2 k = f2s(39.f / 64.f);
+  float2 kB2 = mul2(mul2(k, B), B);
+  float2 kC2 = mul2(mul2(k, C), C);
+  float2 q1 = fma2(f2s(-1.375f), B, A);
+  float2 q2 = fma2(f2s(-0.625f), C, B);
+  float2 q3 = fma2(f2s(-1.375f), C, E);
+  float2 S1 = fma2(q1, q1, kB2);
+  float2 S2 = fma2(q2, q2, kC2);
+  float2 S3 = fma2(q3, q3, kC2);
+  // epsilon = 3/4 (1e-6 max D^2 + floor), the factor of the indicators
   float mid = fmaxf(fmaxf(fabsf(D1), fabsf(D2)), fmaxf(fabsf(D3), fabsf(D4)));
-  float mm = fmaxf(mid, fabsf(D0)), mp = fmaxf(mid, fabsf(D5));
-  const float e6 = 1e-6f * (12.f / 13.f);
-  float iem = rcp_approx(fmaf(e6 * mm, mm, floor_));
-  float iep = rcp_approx(fmaf(e6 * mp, mp, floor_));
-  float a1 = fmaf(Sm1, iem, 1.f), a2 = fmaf(Sm2, iem, 1.f), a3 = fmaf(Sm3, iem, 1.f);
-  float b1 = fmaf(Sp1, iep, 1.f), b2 = fmaf(Sp2, iep, 1.f), b3 = fmaf(Sp3, iep, 1.f);
-  a1 *= a1; a2 *= a2; a3 *= a3;
-  b1 *= b1; b2 *= b2; b3 *= b3;
-  float Pm1 = a2 * a3, Pm2 = a1 * a3, Pm3 = a1 * a2;
-  float Pp1 = b2 * b3, Pp2 = b1 * b3, Pp3 = b1 * b2;
-  // candidates times their linear weights
-  float cm1 = fmaf(0.2f, D0, fmaf(-0.7f, D1, 1.1f * D2));
-  float cm2 = fmaf(3.0f, D2, fmaf(1.2f, D3, -0.6f * D1));
-  float cm3 = fmaf(0.6f, D2, fmaf(1.5f, D3, -0.3f * D4));
-  float cp1 = fmaf(0.2f, D5, fmaf(-0.7f, D4, 1.1f * D3));
-  float cp2 = fmaf(3.0f, D3, fmaf(1.2f, D2, -0.6f * D4));
-  float cp3 = fmaf(0.6f, D3, fmaf(1.5f, D2, -0.3f * D1));
-  float numm = fmaf(Pm1, cm1, fmaf(Pm2, cm2, Pm3 * cm3));
-  float denm = fmaf(0.1f, Pm1, fmaf(0.6f, Pm2, 0.3f * Pm3));
-  float nump = fmaf(Pp1, cp1, fmaf(Pp2, cp2, Pp3 * cp3));
-  float denp = fmaf(0.1f, Pp1, fmaf(0.6f, Pp2, 0.3f * Pp3));
-  pm6h = numm * rcp_approx(denm);
-  pp6h = nump * rcp_approx(denp);
+  float2 m = make_float2(fmaxf(mid, fabsf(D0)), fmaxf(mid, fabsf(D5)));
+  float2 e = fma2(mul2(f2s(0.75e-6f), m), m, f2s(floor_));
+  float2 ie = make_float2(rcp_approx(e.x), rcp_approx(e.y));
+  float2 s1 = fma2(S1, ie, f2s(1.f)), s2 = fma2(S2, ie, f2s(1.f)), s3 = fma2(S3, ie, f2s(1.f));
+  s1 = mul2(mul2(f2s(2.4f), s1), s1);
+  s2 = mul2(s2, s2);
+  s3 = mul2(s3, s3);
+  float2 Q1 = mul2(s2, s3), Q2 = mul2(s1, s3), Q3 = mul2(s1, s2);
+  float2 h1 = fma2(f2s(-0.4f), A, B);
+  float2 h2 = fma2(f2s(0.5f), B, C);
+  float2 h3 = fma2(f2s(-0.25f), E, C);
+  float2 num = fma2(Q1, h1, fma2(Q2, h2, mul2(Q3, h3)));
+  float2 den = fma2(f2s(1.2f), Q1, fma2(f2s(3.f), Q2, mul2(f2s(1.5f), Q3)));
+  float2 w = fma2(num, make_float2(rcp_approx(den.x), rcp_approx(den.y)), X2);
+  pm_h = w.x;
+  pp_h = w.y;
 }
 
 // Per scheme: the stencil radius R and raw one-sided slopes whose scale the
@@ -382,8 +390,8 @@ struct Slopes<5> {
     weno5_pair(v[1] - v[0], v[2] - v[1], v[3] - v[2], v[4] - v[3], v[5] - v[4], v[6] - v[5],
                g.wfloor[d], pm, pp);
   }
-  __device__ __forceinline__ static float half(const DevGrid& g, int d) { return g.hih6[d]; }
-  __device__ __forceinline__ static float half_alpha(const DevGrid& g, int d) { return g.haih6[d]; }
+  __device__ __forceinline__ static float half(const DevGrid& g, int d) { return g.hih[d]; }
+  __device__ __forceinline__ static float half_alpha(const DevGrid& g, int d) { return g.haih[d]; }
 };
 
 // L(src) at node p with multi-index idx; also returns src[p] in `center`.
