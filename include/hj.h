@@ -150,6 +150,19 @@ hj_status hj_set_constraint(hj_grid g, const double* box_lo, const double* box_h
 /* Alternative constraint: the safe region lies outside a ball.
  * l = |x - centre| - radius, with radius > 0. */
 hj_status hj_set_constraint_ball(hj_grid g, const double* centre, double radius);
+/* Constraint given as an array (Sec. II-A: c is the signed distance to the
+ * constraint set C, for any C): l = -c at every node, positive where safe.
+ *   - l holds npts floats, row-major as in hj_get_value; on_device = 1: a
+ *     device pointer, 0: host memory.  The data is copied.
+ *   - It replaces a box or ball; a later hj_set_constraint or
+ *     hj_set_constraint_ball replaces it.
+ *   - The clamp and the initial value read l at the node; migration
+ *     (hj_prolong) reads the fine grid's l.
+ *   - The band_margin option treats every axis as unconstrained.
+ *   - Costs one extra 4-byte read per node in the last RK stage.
+ * HJ_ERR_ARG on NULL or a non-finite value; after that rejection no
+ * constraint is in force (solves fail with HJ_ERR_STATE until one is set). */
+hj_status hj_set_constraint_field(hj_grid g, const float* l, int on_device);
 
 /* Disturbance box D (Sec. II-C): d_j in [d_lo[j], d_hi[j]] for each of the
  * nd inputs.  Asymmetric intervals are allowed; they come from a GP

@@ -22,6 +22,7 @@ MAXD = 6
 MAXIN = 6
 _MODEL = {"drift": 0, "quad_z": 1, "quad_x4": 2}
 _CON = {"box": 0, "ball_out": 1}
+_CON_FIELD = 2
 
 
 class _Problem(ctypes.Structure):
@@ -31,7 +32,8 @@ class _Problem(ctypes.Structure):
                 ("nd", ctypes.c_int), ("d_lo", ctypes.c_double * MAXIN),
                 ("d_hi", ctypes.c_double * MAXIN), ("con_kind", ctypes.c_int),
                 ("con_a", ctypes.c_double * MAXD), ("con_b", ctypes.c_double * MAXD),
-                ("dflo", ctypes.c_void_p), ("dfhi", ctypes.c_void_p)]
+                ("dflo", ctypes.c_void_p), ("dfhi", ctypes.c_void_p),
+                ("lfield", ctypes.c_void_p)]
 
 
 class _Opts(ctypes.Structure):
@@ -94,10 +96,11 @@ def _dp(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-def _problem(spec, dfield=None) -> _Problem:
+def _problem(spec, dfield=None, lfield=None) -> _Problem:
     """ctypes problem for a spec; dfield = (d_lo, d_hi) arrays of shape
-    (nd,) + grid shape for a state-dependent disturbance box (kept alive by
-    the caller for the duration of the call)."""
+    (nd,) + grid shape for a state-dependent disturbance box; lfield = the
+    margin l on the grid, replacing the spec's analytic constraint (arrays
+    kept alive by the caller for the duration of the call)."""
     p = _Problem()
     if dfield is not None:
         p.dflo = dfield[0].ctypes.data
@@ -119,7 +122,19 @@ def _problem(spec, dfield=None) -> _Problem:
         p.con_a[i] = v
     for i, v in enumerate(spec.con_b):
         p.con_b[i] = v
+    if lfield is not None:
+        p.con_kind = _CON_FIELD
+        p.lfield = lfield.ctypes.data
     return p
+
+
+def _lf(spec, lfield):
+    if lfield is None:
+        return None
+    a = np.ascontiguousarray(lfield, dtype=np.float64)
+    if a.size != spec.npts:
+        raise ValueError("lfield must hold one value per node")
+    return a
 
 
 def num_threads() -> int:
@@ -134,10 +149,13 @@ def solve(spec, scheme: int = 5, cfl: float = 0.5, dt: float = 0.0, tol: float =
           check_dt: float = 0.1, max_steps: int = 0, fixed_steps: int = 0,
           clamp: int = 0, warm: Optional[np.ndarray] = None,
           band: float = 0.0, band_margin: int = 0,
-          dfield: Optional[Tuple[np.ndarray, np.ndarray]] = None) -> Tuple[np.ndarray, Dict]:
+          dfield: Optional[Tuple[np.ndarray, np.ndarray]] = None,
+          lfield: Optional[np.ndarray] = None) -> Tuple[np.ndarray, Dict]:
     """Run the oracle solve; returns (W on the grid, stats).  dfield: optional
-    state-dependent disturbance box (d_lo, d_hi), each (nd,) + grid shape."""
+    state-dependent disturbance box (d_lo, d_hi), each (nd,) + grid shape.
+    lfield: optional constraint given as its margin l on the grid."""
     dfield = _field(dfield)
+    lfield = _lf(spec, lfield)
     W = np.zeros(spec.n, dtype=np.float64)
     if warm is not None:
         W[...] = warm
@@ -145,7 +163,7 @@ def solve(spec, scheme: int = 5, cfl: float = 0.5, dt: float = 0.0, tol: float =
               fixed_steps=fixed_steps, clamp=clamp, warm=1 if warm is not None else 0,
               band=band, band_margin=band_margin)
     st = _Stats()
-    pr = _problem(spec, dfield)
+    pr = _problem(spec, dfield, lfield)
     rc = lib().or_solve(ctypes.byref(pr), ctypes.byref(o), _dp(W), ctypes.byref(st))
     if rc < 0:
         raise ValueError("oracle rejected the problem")
@@ -181,9 +199,10 @@ def hamiltonian(spec, x: Sequence[float], p: Sequence[float]) -> float:
     return lib().or_hamiltonian(ctypes.byref(pr), _dp(xa), _dp(pa))
 
 
-def margin(spec) -> np.ndarray:
+def margin(spec, lfield=None) -> np.ndarray:
     out = np.zeros(spec.n, dtype=np.float64)
-    pr = _problem(spec)
+    lfield = _lf(spec, lfield)
+    pr = _problem(spec, None, lfield)
     lib().or_fill_margin(ctypes.byref(pr), _dp(out))
     return out
 
@@ -210,10 +229,11 @@ def rhs(spec, scheme: int, W: np.ndarray) -> np.ndarray:
     return out
 
 
-def prolong(coarse, Wc: np.ndarray, fine) -> np.ndarray:
+def prolong(coarse, Wc: np.ndarray, fine, lfield_fine=None) -> np.ndarray:
     Wc = np.ascontiguousarray(Wc, dtype=np.float64)
     Wf = np.zeros(fine.n, dtype=np.float64)
-    pc, pf = _problem(coarse), _problem(fine)
+    lfield_fine = _lf(fine, lfield_fine)
+    pc, pf = _problem(coarse), _problem(fine, None, lfield_fine)
     if lib().or_prolong(ctypes.byref(pc), _dp(Wc), ctypes.byref(pf), _dp(Wf)) != 0:
         raise ValueError("fine grid not inside coarse grid")
     return Wf

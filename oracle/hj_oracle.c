@@ -66,6 +66,7 @@
 /* constraint shapes: margin l = -c with c the signed distance of Sec. II-A */
 #define OR_CON_BOX 0       /* safe inside an axis-aligned box (+-inf = free axis) */
 #define OR_CON_BALL_OUT 1  /* safe outside a ball                                 */
+#define OR_CON_FIELD 2     /* margin l given node by node (lfield)                */
 
 #define OR_CLAMP_VI 0
 #define OR_CLAMP_MONOTONE 1
@@ -85,6 +86,7 @@ typedef struct {
   double con_b[OR_MAXD];  /* box hi, or ball radius in con_b[0]                  */
   const double* dflo;     /* state-dependent disturbance box (Sec. II-C): input  */
   const double* dfhi;     /* j's bound at node k is [j * npts + k]; NULL = box   */
+  const double* lfield;   /* OR_CON_FIELD: the margin l = -c at every node       */
 } or_problem;
 
 typedef struct {
@@ -406,7 +408,7 @@ static void fill_margin(const or_problem* P, double* l) {
     double x[OR_MAXD];
     grid_unravel(P, pt, idx);
     grid_coords(P, idx, x);
-    l[pt] = or_margin(P, x);
+    l[pt] = P->con_kind == OR_CON_FIELD ? P->lfield[pt] : or_margin(P, x);
   }
 }
 
@@ -553,7 +555,7 @@ int or_prolong(const or_problem* C, const double* Wc, const or_problem* Fp, doub
     grid_unravel(Fp, pt, idx);
     grid_coords(Fp, idx, x);
     if (interp(C, Wc, x, &v) != 0) { bad |= 1; continue; }
-    Wf[pt] = fmin(v, or_margin(Fp, x));
+    Wf[pt] = fmin(v, Fp->con_kind == OR_CON_FIELD ? Fp->lfield[pt] : or_margin(Fp, x));
   }
   return bad ? -1 : 0;
 }

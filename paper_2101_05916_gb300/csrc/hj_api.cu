@@ -84,6 +84,7 @@ hjd::DevGrid devgrid(const hj_grid g) {
   }
   for (int i = 0; i < HJ_MAX_DIM; ++i) d.alpha[i] = g->alpha[i];
   d.tab = g->tab;
+  if (g->con_kind == hjd::C_FIELD) d.lfield = g->lfield;
   if (g->dfield_nd > 0) {
     d.dflo = g->dfield;
     d.dfhi = g->dfield + (size_t)g->dfield_nd * (size_t)g->npts;
@@ -328,6 +329,7 @@ void hj_grid_destroy(hj_grid g) {
     for (int i = 0; i < 4; ++i) cudaFree(g->raw[i]);
     cudaFree(g->tab);
     cudaFree(g->dfield);
+    cudaFree(g->lfield);
     cudaFree(g->dscal);
     cudaFree(g->qbuf);
     if (g->hscal) cudaFreeHost(g->hscal);
@@ -442,6 +444,14 @@ hj_status hj_set_dynamics(hj_grid g, int model, const double* params, int nparam
   return HJ_OK;
 }
 
+static void drop_lfield(hj_grid g) {
+  if (g->lfield) {
+    DeviceGuard dg(g->device);
+    cudaFree(g->lfield);
+    g->lfield = nullptr;
+  }
+}
+
 hj_status hj_set_constraint(hj_grid g, const double* box_lo, const double* box_hi) {
   if (!g) return fail(HJ_ERR_ARG, "grid is NULL");
   if (!box_lo || !box_hi) return fail(HJ_ERR_ARG, "box is NULL");
@@ -452,6 +462,7 @@ hj_status hj_set_constraint(hj_grid g, const double* box_lo, const double* box_h
     if (!(std::isinf(box_lo[i]) && std::isinf(box_hi[i]))) constrained++;
   }
   if (!constrained) return fail(HJ_ERR_ARG, "no axis is constrained");
+  drop_lfield(g);
   g->con_kind = hjd::C_BOX;
   for (int i = 0; i < g->ndim; ++i) {
     g->ca[i] = box_lo[i];
@@ -465,6 +476,9 @@ hj_status hj_set_constraint_ball(hj_grid g, const double* centre, double radius)
   if (!g) return fail(HJ_ERR_ARG, "grid is NULL");
   if (!centre || !(radius > 0.0) || !std::isfinite(radius))
     return fail(HJ_ERR_ARG, "need a centre and a finite radius > 0");
+  for (int i = 0; i < g->ndim; ++i)
+    if (!std::isfinite(centre[i])) return fail(HJ_ERR_ARG, "centre must be finite");
+  drop_lfield(g);
   g->con_kind = hjd::C_BALL_OUT;
   for (int i = 0; i < g->ndim; ++i) {
     if (!std::isfinite(centre[i])) return fail(HJ_ERR_ARG, "centre must be finite");
@@ -472,6 +486,31 @@ hj_status hj_set_constraint_ball(hj_grid g, const double* centre, double radius)
     g->cb[i] = 0.0;
   }
   g->cb[0] = radius;
+  drop_graph(g);
+  return HJ_OK;
+}
+
+hj_status hj_set_constraint_field(hj_grid g, const float* l, int on_device) {
+  if (!g || !l) return fail(HJ_ERR_ARG, "NULL argument");
+  DeviceGuard dg(g->device);
+  size_t n = (size_t)g->npts;
+  if (!g->lfield) HJ_CU(cudaMalloc(&g->lfield, n * sizeof(float)));
+  cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  HJ_CU(cudaMemcpyAsync(g->lfield, l, n * sizeof(float), k, g->stream));
+  HJ_CU(cudaMemsetAsync(g->dscal + 5, 0, sizeof(unsigned), g->stream));
+  HJ_CU(hjk::launch_field_check(g->lfield, g->lfield, (long long)n, (int*)(g->dscal + 5),
+                                g->stream));
+  HJ_CU(cudaMemcpyAsync(g->hscal + 5, g->dscal + 5, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                        g->stream));
+  HJ_CU(cudaStreamSynchronize(g->stream));
+  if (g->hscal[5]) {
+    // the rejected values are gone with the buffer; no constraint is in force now
+    drop_lfield(g);
+    g->con_kind = -1;
+    drop_graph(g);
+    return fail(HJ_ERR_ARG, "constraint field: every value must be finite");
+  }
+  g->con_kind = hjd::C_FIELD;
   drop_graph(g);
   return HJ_OK;
 }

@@ -21,7 +21,7 @@ namespace hjd {
 
 constexpr int MAXD = 4;
 enum { M_DRIFT = 0, M_QUAD_Z = 1, M_QUAD_X4 = 2 };
-enum { C_BOX = 0, C_BALL_OUT = 1 };
+enum { C_BOX = 0, C_BALL_OUT = 1, C_FIELD = 2 };
 
 // Everything a kernel needs to know about one grid, passed by value.
 struct DevGrid {
@@ -51,6 +51,7 @@ struct DevGrid {
   const float* tab;    // quad_x4: g * tan(th_j) per th index
   const float* dflo;   // state-dependent disturbance box, input-major nd x npts
   const float* dfhi;   // (nullptr: the uniform box dlo/dhi)
+  const float* lfield; // C_FIELD: the margin l at every node
 };
 
 // Arguments of one Runge-Kutta stage launch.
@@ -83,10 +84,12 @@ __device__ __forceinline__ int fast_div(int q, unsigned m, int s) {
 
 // ---------------------------------------------------------------- geometry
 
-// Margin l = -c to the constraint set: distance to the nearest face inside a
-// box, minus the Euclidean distance outside it; or distance outside a ball.
+// Margin l = -c to the constraint set at node p, coordinates x: distance to
+// the nearest face inside a box, minus the Euclidean distance outside it;
+// distance outside a ball; or the caller's value at the node.
 template <int D>
-__device__ __forceinline__ float margin(const DevGrid& g, const float (&x)[D]) {
+__device__ __forceinline__ float margin(const DevGrid& g, const float (&x)[D], int p) {
+  if (g.con_kind == C_FIELD) return __ldg(g.lfield + p);
   if (g.con_kind == C_BALL_OUT) {
     float s = 0.f;
 #pragma unroll

@@ -33,6 +33,7 @@ struct hj_grid_s {
   float* tab = nullptr;    // per-index coefficient table of the model
   float* dfield = nullptr; // state-dependent disturbance box: lo (nd x npts), then hi
   int dfield_nd = 0;       // inputs in dfield (0: the uniform box is in force)
+  float* lfield = nullptr; // constraint margin l at every node (constraint kind C_FIELD)
   unsigned* dscal = nullptr;  // device scalars: [0..3] alpha bits, [4] residual bits, [5] flag
   unsigned* hscal = nullptr;  // pinned host mirror of dscal
   double* qbuf = nullptr;     // query staging (device)

@@ -78,7 +78,7 @@ __global__ void init_kernel(const DevGrid g, float* W, float* snap, int warm) {
     float x[D];
     unravel<D>(g, pt, idx);
     coords<D>(g, idx, x);
-    float l = hjd::margin<D>(g, x);
+    float l = hjd::margin<D>(g, x, pt);
     float w = warm ? fminf(W[pt], l) : l;
     W[pt] = w;
     snap[pt] = w;
@@ -131,7 +131,7 @@ __global__ void prolong_kernel(const DevGrid c, const float* __restrict__ Wc, co
       }
       acc += wgt * (double)__ldg(Wc + off);
     }
-    Wf[pt] = fminf((float)acc, hjd::margin<D>(f, xf));
+    Wf[pt] = fminf((float)acc, hjd::margin<D>(f, xf, pt));
   }
 }
 

@@ -68,7 +68,7 @@ __device__ __forceinline__ unsigned stage_point(const DevGrid& g, const StageArg
   } else {
     float w = a.base[p];
     float w3 = fmaf(1.f / 3.f, w, (2.f / 3.f) * stepped);
-    float wn = fminf(w3, margin<D>(g, x));
+    float wn = fminf(w3, margin<D>(g, x, p));
     if (a.clamp) wn = fminf(wn, w);
     if (w3 != w3) wn = w3;  // keep a NaN visible to the stop test
     a.dst[p] = wn;

@@ -64,7 +64,7 @@ __global__ void static_init_kernel(const hjd::DevGrid g, float* W, int warm) {
     idx[0] = r;
     float x[D];
     hjd::coords<D>(g, idx, x);
-    float l = hjd::margin<D>(g, x);
+    float l = hjd::margin<D>(g, x, pt);
     W[pt] = warm ? fminf(W[pt], l) : l;
   }
 }

@@ -91,6 +91,7 @@ SIGNATURES = {
     "hj_set_dynamics": (_i, [_vp, _i, _P(_d), _i]),
     "hj_set_constraint": (_i, [_vp, _P(_d), _P(_d)]),
     "hj_set_constraint_ball": (_i, [_vp, _P(_d), _d]),
+    "hj_set_constraint_field": (_i, [_vp, _vp, _i]),
     "hj_set_disturbance_bound": (_i, [_vp, _P(_d), _P(_d), _i]),
     "hj_set_disturbance_field": (_i, [_vp, _vp, _vp, _i, _i]),
     "hj_solve": (_i, [_vp, _i, _P(hj_solve_opts), _P(hj_solve_stats)]),
@@ -202,6 +203,25 @@ def hj_set_constraint(g: int, box_lo: Sequence[float], box_hi: Sequence[float]) 
 
 def hj_set_constraint_ball(g: int, centre: Sequence[float], radius: float) -> None:
     _check(lib().hj_set_constraint_ball(g, _darr(centre), float(radius)))
+
+
+def hj_set_constraint_field(g: int, l) -> None:
+    """Constraint as its margin l on the grid: numpy array with one value per
+    node (host), or a flat float32 CUDA tensor of npts values."""
+    npts = lib().hj_grid_points(g)
+    try:
+        import torch
+        if isinstance(l, torch.Tensor):
+            if l.numel() != npts:
+                raise ValueError("l must hold one value per node")
+            _check(lib().hj_set_constraint_field(g, l.data_ptr(), 1))
+            return
+    except ImportError:  # pragma: no cover
+        pass
+    a = np.ascontiguousarray(l, dtype=np.float32)
+    if a.size != npts:
+        raise ValueError("l must hold one value per node")
+    _check(lib().hj_set_constraint_field(g, a.ctypes.data, 0))
 
 
 def hj_set_disturbance_bound(g: int, d_lo: Sequence[float], d_hi: Sequence[float]) -> None:
@@ -481,6 +501,9 @@ class Grid:
 
     def set_disturbance_field(self, d_lo, d_hi) -> None:
         hj_set_disturbance_field(self.handle, d_lo, d_hi)
+
+    def set_constraint_field(self, l) -> None:
+        hj_set_constraint_field(self.handle, l)
 
     def solve(self, mode: int = HJ_COLD, **kw) -> Dict:
         rc, st = hj_solve(self.handle, mode, make_opts(**kw))

@@ -113,6 +113,34 @@ def drift(n: Sequence[int], half: float, b: float, con_kind: str = CON_BOX,
                        con_kind=con_kind, con_a=ca, con_b=cb)
 
 
+def demo10d_x(n: int = 31, b: float = 0.5, name: str = "x") -> ProblemSpec:
+    """x (or y) subsystem under the 10-D demo's constraint boxes (Sec. V):
+    |p| <= 2.5, |v| <= 3.5 and |theta| <= pi/8 together, on a grid that holds
+    the box with a margin: [-3.5,3.5] x [-4.5,4.5] x [-0.5,0.5] x [-2,2]."""
+    t = math.pi / 8.0
+    return ProblemSpec(name=name, n=(n,) * 4, lo=(-3.5, -4.5, -0.5, -2.0),
+                       hi=(3.5, 4.5, 0.5, 2.0), model=QUAD_X4, params=X4_PARAMS,
+                       d_lo=(-b,), d_hi=(b,), con_kind=CON_BOX,
+                       con_a=(-2.5, -3.5, -t, -INF), con_b=(2.5, 3.5, t, INF))
+
+
+def demo10d_z(n: int = 101, b: float = 0.5) -> ProblemSpec:
+    """z subsystem under the 10-D demo's boxes (Sec. V): z in [0.35, 2.8] and
+    |v_z| <= 3.5, on [0, 3.2] x [-4.5, 4.5]."""
+    return ProblemSpec(name="z", n=(n, n), lo=(0.0, -4.5), hi=(3.2, 4.5), model=QUAD_Z,
+                       params=Z_PARAMS, d_lo=(-b,), d_hi=(b,), con_kind=CON_BOX,
+                       con_a=(0.35, -3.5), con_b=(2.8, 3.5))
+
+
+def two_band_margin(spec: ProblemSpec, bands: Sequence[Tuple[float, float]],
+                    axis: int = 0) -> np.ndarray:
+    """Margin l of a non-convex safe set: the union of slabs lo <= x_axis <= hi
+    (distance to the nearest face of the slab the node lies in, else minus the
+    distance to the nearest slab), on every node of the grid."""
+    xs = np.meshgrid(*spec.coords(), indexing="ij")[axis]
+    return np.max([np.minimum(xs - lo, hi - xs) for lo, hi in bands], axis=0)
+
+
 # ---------------------------------------------------------------- configs
 
 def config0() -> ProblemSpec:

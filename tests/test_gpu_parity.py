@@ -118,6 +118,79 @@ def test_state_dependent_bound_parity(hj, name, make, scheme, steps, axis, centr
     assert_parity(Wg, Wo, spec)
 
 
+@pytest.mark.parametrize("name,make,scheme,steps", [
+    ("demo10d_x17", lambda: wl.demo10d_x(17, 0.5), 5, 10),
+    ("demo10d_z101", lambda: wl.demo10d_z(101, 0.5), 2, 60),
+])
+def test_multi_axis_box_parity(hj, name, make, scheme, steps):
+    """The 10-D demo's constraint boxes span several axes of a subsystem."""
+    spec = make()
+    dt = oracle.cfl_dt(spec)
+    Wo, _ = oracle.solve(spec, scheme=scheme, dt=dt, fixed_steps=steps)
+    Wg, st = gpu_fixed(hj, spec, scheme, steps, dt=dt)
+    assert_parity(Wg, Wo, spec)
+
+
+def test_constraint_field_parity(hj):
+    """Non-convex safe set given as an array: z in [0.5, 1.4] or [1.6, 2.5]."""
+    spec = wl.quad_z(101, 0.5)
+    l = wl.two_band_margin(spec, [(0.5, 1.4), (1.6, 2.5)])
+    dt = oracle.cfl_dt(spec)
+    g = hj.Grid.from_spec(spec)
+    g.set_constraint_field(l)
+    for scheme, steps in ((5, 60), (2, 60)):
+        Wo, _ = oracle.solve(spec, scheme=scheme, dt=dt, fixed_steps=steps, lfield=l)
+        g.solve(hj.HJ_COLD, scheme=scheme, dt=dt, fixed_steps=steps)
+        assert_parity(g.value(), Wo, spec)
+    # converged at 1e-4 per window, ENO2 with the VI clamp (stencil switching
+    # at the inner faces holds the residual near 1e-5, so no tighter stop);
+    # W is compared with the oracle at the GPU's own stop step
+    Wo, sto = oracle.solve(spec, scheme=2, dt=dt, tol=1e-4, max_steps=50000, lfield=l)
+    st = g.solve(hj.HJ_COLD, scheme=2, dt=dt, tol=1e-4)
+    assert st["converged"] and sto["converged"]
+    assert abs(st["windows"] - sto["windows"]) <= 6
+    Wc = g.value()
+    Wt, _ = oracle.solve(spec, scheme=2, dt=dt, fixed_steps=st["steps"], lfield=l)
+    assert_parity(Wc, Wt, spec)
+    # the gap between the bands is never safe, and W <= l everywhere
+    assert np.all(Wc <= l.astype(np.float32) + 1e-6)
+    z = spec.coords()[0]
+    assert np.all(Wc[(z > 1.4) & (z < 1.6)] < 0)
+    # a box afterwards replaces the array
+    g.solve(hj.HJ_COLD, scheme=2, dt=dt, fixed_steps=5)
+    hj.hj_set_constraint(g.handle, spec.con_a, spec.con_b)
+    g.solve(hj.HJ_COLD, scheme=2, dt=dt, fixed_steps=5)
+    Wb = g.value()
+    Wo, _ = oracle.solve(spec, scheme=2, dt=dt, fixed_steps=5)
+    assert_parity(Wb, Wo, spec)
+    g.close()
+
+
+def test_constraint_field_prolong_and_errors(hj):
+    cs, fs = wl.quad_z(51, 0.5), wl.quad_z(101, 0.5)
+    lc = wl.two_band_margin(cs, [(0.5, 1.4), (1.6, 2.5)])
+    lf = wl.two_band_margin(fs, [(0.5, 1.4), (1.6, 2.5)])
+    gc, gf = hj.Grid.from_spec(cs), hj.Grid.from_spec(fs)
+    gc.set_constraint_field(lc)
+    gf.set_constraint_field(lf)
+    gc.solve(hj.HJ_COLD, scheme=2, fixed_steps=40)
+    Wc = gc.value()
+    hj.prolong(gc, gf)
+    Wo = oracle.prolong(cs, Wc.astype(np.float64), fs, lfield_fine=lf)
+    assert np.abs(gf.value() - Wo).max() <= 1e-5 * np.abs(Wo).max()
+    with pytest.raises(ValueError):
+        gf.set_constraint_field(lf[:10])
+    bad = lf.copy()
+    bad[3, 4] = np.inf
+    with pytest.raises(hj.HJError):
+        gf.set_constraint_field(bad)
+    with pytest.raises(hj.HJError) as e:
+        gf.solve(hj.HJ_COLD, scheme=2, fixed_steps=2)
+    assert e.value.status == hj.HJ_ERR_STATE
+    gc.close()
+    gf.close()
+
+
 def test_monotone_clamp_parity(hj):
     spec = wl.quad_z(61, 0.8)
     dt = oracle.cfl_dt(spec)

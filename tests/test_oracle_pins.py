@@ -258,6 +258,48 @@ def test_drift_1d_state_dependent_bound_closed_form(scheme):
     assert np.abs(W - exact)[away & (np.abs(x) < 1.9)].max() < 0.05 * h
 
 
+@pytest.mark.parametrize("scheme", [2, 5])
+def test_constraint_field_two_intervals_is_the_window_minimum(scheme):
+    """Constraint given as an array (Sec. II-A, c for an arbitrary set C):
+    a non-convex safe set, the union |x - 1| <= 0.5 or |x + 1.1| <= 0.6.
+    With dx/dt = d, |d| <= b and no control, every point of
+    [x - b s, x + b s] is reachable, so W(x, s) is the minimum of l over that
+    window (found here by dense sampling)."""
+    b, T = 0.4, 0.5
+    s = wl.drift((241,), 2.5, b, wl.CON_BOX, r=1.0)
+    x = s.coords()[0]
+
+    def l_of(y):
+        return np.maximum(0.5 - np.abs(y - 1.0), 0.6 - np.abs(y + 1.1))
+
+    W, _ = oracle.solve(s, scheme=scheme, dt=T / 100, fixed_steps=100, lfield=l_of(x))
+    ys = np.linspace(-b * T, b * T, 4001)
+    exact = np.array([l_of(xi + ys).min() for xi in x])
+    h = s.h()[0]
+    inner = np.abs(x) < 2.5 - 6 * h
+    assert np.abs(W - exact)[inner].max() < 2.0 * h
+    # away from the kinks of the exact value the scheme is much closer: l
+    # peaks at 1 and -1.1 and bottoms out at 0 in the gap, so the window
+    # minimum has kinks at 1, -1.1 and +-b T
+    kinks = np.array([1.0, -1.1, b * T, -b * T])
+    far = inner & (np.abs(x[:, None] - kinks[None, :]).min(axis=1) > 12 * h)
+    assert np.abs(W - exact)[far].max() < 1e-3 * h
+    # the two pieces stay apart: the gap between them is unsafe
+    assert W[np.argmin(np.abs(x + 0.2))] < 0
+
+
+def test_constraint_field_equals_the_analytic_ball():
+    """The same margin given as an array gives the same W as the analytic
+    ball, and the closed form of the 1-D erosion."""
+    s = wl.drift((37,), 2.0, 0.5, wl.CON_BALL_OUT, r=0.3)
+    x = s.coords()[0]
+    l = np.abs(x) - 0.3
+    Wa, _ = oracle.solve(s, scheme=5, fixed_steps=20)
+    Wf, _ = oracle.solve(s, scheme=5, fixed_steps=20, lfield=l)
+    assert np.array_equal(Wa, Wf)
+    assert np.array_equal(oracle.margin(s, l), l)
+
+
 def test_uniform_field_equals_box():
     s = wl.quad_x4(9, 0.6)
     W0, _ = oracle.solve(s, scheme=5, fixed_steps=4)
