@@ -341,6 +341,38 @@ hj_status hj_server_get_stats(hj_server s, hj_server_stats* out);
 enum { HJ_ORDER_FIFO = 0, HJ_ORDER_SHORTEST = 1 };
 hj_status hj_server_set_policy(hj_server s, int order, long long max_active_nodes);
 
+/* Safety filter of the safe-learning loop (Sec. II-B, II-C) for a system
+ * decomposed into independent subsystem grids (Sec. III-A, e.g. the 10-D
+ * quadcopter as x, y and z).  For each of nq full states:
+ *   - Grid k sees the subsystem state x_k[d] = states[q * state_dim +
+ *     axes[k * HJ_MAX_DIM + d]] for d < its ndim; W_k(x_k) and grad W_k are
+ *     multilinear interpolations of the node values and of the node
+ *     gradients (central differences, one-sided at the ends), in double.
+ *   - The decomposed value is w_out[q] = min_k W_k (valid for separable
+ *     constraint boxes).
+ *   - Where W_k <= level, the control ctrl_index[k] is replaced by the
+ *     optimal safety control u* = argmax_u min_d <grad W_k, f_k> (Sec. II-A;
+ *     W = -V): the input's upper bound where grad W_k . df/du > 0, the lower
+ *     where it is < 0; on a tie the performance control stays, clipped to
+ *     the input box.  level = 0 switches on the boundary; level > 0 keeps a
+ *     margin, e.g. the contracted sublevel set of the previous value
+ *     function while an update runs (Sec. II-C).
+ *   - active_out[q] has bit k set where grid k's safety control was applied.
+ *   - Other controls copy u_perf.  ctrl_index[k] = -1: the grid drives no
+ *     control (HJ_DRIFT has none).  No control may be driven by two grids.
+ * Layout: states nq x state_dim, u_perf and u_out nq x ctrl_dim (doubles,
+ * row-major); w_out nq doubles; active_out nq ints.  on_device = 1: all
+ * buffers are device memory; 0: host memory, staged through a device block
+ * and a pinned host block that grids[0] keeps for later calls (one copy in,
+ * one copy out).  Runs on grids[0]'s stream; every grid must hold a value
+ * and live on the same device; calls sharing grids[0] must not overlap.
+ * HJ_ERR_ARG on bad indices or dimensions, or a state outside a grid's box
+ * (the outputs are then undefined); HJ_ERR_STATE for a grid without value. */
+hj_status hj_safety_filter(const hj_grid* grids, int ngrids, const int* axes,
+                           const int* ctrl_index, int state_dim, int ctrl_dim, long long nq,
+                           const double* states, const double* u_perf, double level,
+                           double* u_out, double* w_out, int* active_out, int on_device);
+
 /* Allocation-free fixed-horizon solve.  The paper has no counterpart: this
  * entry point exists for callers that must not allocate device memory after
  * start-up.  One example is a real-time safety filter running beside a

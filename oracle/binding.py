@@ -259,6 +259,50 @@ def query_gradient(spec, W: np.ndarray, xs: np.ndarray) -> np.ndarray:
     return out
 
 
+# ------------------------------------------------------------------ safety filter
+
+def control_gain(spec) -> Tuple[np.ndarray, float, float]:
+    """df/du of the subsystem's single input and its box, from the model
+    definitions: z has dv/dt = kT u - g + d, x/y have dw/dt = -d0 th + n0 u.
+    A drift has no input (gain 0)."""
+    b = np.zeros(spec.ndim)
+    if spec.model == "quad_z":
+        b[1] = spec.params[0]
+        return b, spec.params[2], spec.params[3]
+    if spec.model == "quad_x4":
+        b[3] = spec.params[3]
+        return b, spec.params[4], spec.params[5]
+    return b, 0.0, 0.0
+
+
+def safety_filter(specs, Ws, axes, ctrl_index, states: np.ndarray, u_perf: np.ndarray,
+                  level: float = 0.0):
+    """Safe-learning switch over decomposed subsystems (Sec. II-A, II-B, III-A):
+    W = min_k W_k; where W_k <= level the control of subsystem k becomes
+    argmax_u min_d <grad W_k, f_k> (bang-bang; a tie keeps the performance
+    control, clipped to the input box).  Returns (u, w, active mask)."""
+    states = np.asarray(states, dtype=np.float64)
+    u = np.array(u_perf, dtype=np.float64, copy=True)
+    nq = states.shape[0]
+    w = np.full(nq, np.inf)
+    active = np.zeros(nq, dtype=np.int64)
+    for k, (spec, W) in enumerate(zip(specs, Ws)):
+        xs = states[:, list(axes[k][:spec.ndim])]
+        wk = query_value(spec, W, xs)
+        gk = query_gradient(spec, W, xs)
+        w = np.minimum(w, wk)
+        b, ulo, uhi = control_gain(spec)
+        c = ctrl_index[k]
+        if c < 0 or not b.any():
+            continue
+        s = gk @ b
+        on = wk <= level
+        us = np.where(s > 0, uhi, np.where(s < 0, ulo, np.clip(u[:, c], ulo, uhi)))
+        u[on, c] = us[on]
+        active[on] |= 1 << k
+    return u, w, active
+
+
 # ------------------------------------------------------------------ brute force
 
 def _z_arc_extremes(z0, v0, a, tau):
@@ -344,5 +388,5 @@ def z_closed_form(z: np.ndarray, v: np.ndarray, kT: float, g: float, u_hi: float
 
 __all__ = ["build", "lib", "solve", "alpha", "cfl_dt", "hamiltonian", "margin", "margin_at",
            "line_slopes", "rhs", "prolong", "query_value", "query_gradient", "brute_force_z",
-           "z_closed_form", "num_threads", "set_num_threads"]
+           "z_closed_form", "num_threads", "set_num_threads", "control_gain", "safety_filter"]
 

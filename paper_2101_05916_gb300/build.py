@@ -18,7 +18,8 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "libhj_gb300.so")
 BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["hj_kernels.cu", "hj_api.cu", "hj_batch.cu", "hj_server.cu", "hj_static.cu"]
+SOURCES = ["hj_kernels.cu", "hj_api.cu", "hj_batch.cu", "hj_server.cu", "hj_static.cu",
+           "hj_filter.cu"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-ftz=true",
          "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]
 

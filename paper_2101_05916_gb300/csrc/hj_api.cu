@@ -61,6 +61,8 @@ hjd::DevGrid devgrid(const hj_grid g) {
     d.h[i] = (float)g->h[i];
     d.lo_d[i] = g->lo[i];
     d.h_d[i] = g->h[i];
+    d.ih_d[i] = 1.0 / g->h[i];
+    d.ih2_d[i] = 0.5 / g->h[i];
     d.ih[i] = (float)(1.0 / g->h[i]);
     // WENO epsilon floor: 1e-18 in divided differences, on undivided ones
     // times h^2, times the 3/4 scale of the smoothness indicators
@@ -332,6 +334,8 @@ void hj_grid_destroy(hj_grid g) {
     cudaFree(g->lfield);
     cudaFree(g->dscal);
     cudaFree(g->qbuf);
+    cudaFree(g->fdev);
+    if (g->fhost) cudaFreeHost(g->fhost);
     if (g->hscal) cudaFreeHost(g->hscal);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
   }

@@ -37,6 +37,8 @@ struct DevGrid {
   float h[MAXD];
   double lo_d[MAXD];   // the same box in double, for interpolation
   double h_d[MAXD];
+  double ih_d[MAXD];   // 1 / h in double
+  double ih2_d[MAXD];  // 1 / (2 h) in double
   float ih[MAXD];      // 1 / h
   float hih[MAXD];     // 0.5 / h
   float haih[MAXD];    // 0.5 a / h
@@ -205,6 +207,33 @@ __device__ __forceinline__ void abs_f_max(const DevGrid& g, const float (&x)[D],
       m[d] = fmaxf(m[d], fmaxf(fabsf(dl), fabsf(dh)));
     }
   }
+}
+
+// ------------------------------------------------------- interpolation
+
+// Coarse cell and fractional offset of coordinate xv along axis d of grid c.
+__device__ __forceinline__ bool locate(const DevGrid& c, int d, double xv, int& i0, double& fr) {
+  double t = (xv - c.lo_d[d]) * c.ih_d[d];
+  double tol = 1e-9;
+  if (t < -tol || t > (double)(c.n[d] - 1) + tol) return false;
+  int i = (int)floor(t);
+  i = min(max(i, 0), c.n[d] - 2);
+  double f = t - (double)i;
+  fr = fmin(fmax(f, 0.0), 1.0);
+  i0 = i;
+  return true;
+}
+
+// Twice the node gradient along axis d, times h: the central difference
+// inside, twice the one-sided difference at the ends.  Times 1 / (2 h) it is
+// the node gradient.
+template <int D>
+__device__ __forceinline__ double node_diff2(const DevGrid& g, const float* W, int off, int i,
+                                             int d) {
+  int s = g.stride[d];
+  if (i == 0) return 2.0 * ((double)W[off + s] - (double)W[off]);
+  if (i == g.n[d] - 1) return 2.0 * ((double)W[off] - (double)W[off - s]);
+  return (double)W[off + s] - (double)W[off - s];
 }
 
 // ---------------------------------------------------------- grid lines

@@ -38,6 +38,9 @@ struct hj_grid_s {
   unsigned* hscal = nullptr;  // pinned host mirror of dscal
   double* qbuf = nullptr;     // query staging (device)
   size_t qcap = 0;
+  double* fdev = nullptr;     // safety-filter staging: device block ...
+  double* fhost = nullptr;    // ... and its pinned host mirror
+  size_t fcap = 0;            // doubles in each
 
   bool has_value = false;
   bool alpha_valid = false;

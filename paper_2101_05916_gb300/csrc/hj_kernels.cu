@@ -51,6 +51,8 @@ __device__ __forceinline__ void unravel(const DevGrid& g, int pt, int (&idx)[D])
 }
 
 using hjd::coords;
+using hjd::locate;
+using hjd::node_diff2;
 
 template <int D, int M>
 __global__ void alpha_kernel(const DevGrid g, unsigned* out) {
@@ -85,18 +87,6 @@ __global__ void init_kernel(const DevGrid g, float* W, float* snap, int warm) {
   }
 }
 
-// Coarse cell and fractional offset of coordinate xv along axis d of grid c.
-__device__ __forceinline__ bool locate(const DevGrid& c, int d, double xv, int& i0, double& fr) {
-  double t = (xv - c.lo_d[d]) / c.h_d[d];
-  double tol = 1e-9;
-  if (t < -tol || t > (double)(c.n[d] - 1) + tol) return false;
-  int i = (int)floor(t);
-  i = min(max(i, 0), c.n[d] - 2);
-  double f = t - (double)i;
-  fr = fmin(fmax(f, 0.0), 1.0);
-  i0 = i;
-  return true;
-}
 
 template <int D>
 __global__ void prolong_kernel(const DevGrid c, const float* __restrict__ Wc, const DevGrid f,
@@ -135,14 +125,6 @@ __global__ void prolong_kernel(const DevGrid c, const float* __restrict__ Wc, co
   }
 }
 
-// Node gradient along axis d: central difference, one-sided at the ends.
-template <int D>
-__device__ __forceinline__ double node_grad(const DevGrid& g, const float* W, int off, int i, int d) {
-  int s = g.stride[d];
-  if (i == 0) return ((double)W[off + s] - (double)W[off]) / g.h_d[d];
-  if (i == g.n[d] - 1) return ((double)W[off] - (double)W[off - s]) / g.h_d[d];
-  return ((double)W[off + s] - (double)W[off - s]) / (2.0 * g.h_d[d]);
-}
 
 template <int D>
 __global__ void query_kernel(const DevGrid g, const float* __restrict__ W, int npts,
@@ -175,14 +157,14 @@ __global__ void query_kernel(const DevGrid g, const float* __restrict__ W, int n
     }
     if (grad) {
 #pragma unroll
-      for (int d = 0; d < D; ++d) acc[d] += wgt * node_grad<D>(g, W, off, ci[d], d);
+      for (int d = 0; d < D; ++d) acc[d] += wgt * node_diff2<D>(g, W, off, ci[d], d);
     } else {
       acc[0] += wgt * (double)W[off];
     }
   }
   if (grad) {
 #pragma unroll
-    for (int d = 0; d < D; ++d) out[k * D + d] = acc[d];
+    for (int d = 0; d < D; ++d) out[k * D + d] = acc[d] * g.ih2_d[d];
   } else {
     out[k] = acc[0];
   }

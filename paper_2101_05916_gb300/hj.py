@@ -102,6 +102,8 @@ SIGNATURES = {
     "hj_get_value": (_i, [_vp, _vp, _i]),
     "hj_query_value": (_i, [_vp, _i, _P(_d), _P(_d)]),
     "hj_query_gradient": (_i, [_vp, _i, _P(_d), _P(_d)]),
+    "hj_safety_filter": (_i, [_P(_vp), _i, _P(_i), _P(_i), _i, _i, ctypes.c_longlong, _vp, _vp,
+                              _d, _vp, _vp, _vp, _i]),
     "hj_alpha": (_i, [_vp, _P(_d)]),
     "hj_autotune": (_i, [_vp, _i, _P(_i)]),
     "hj_grid_points": (_ll, [_vp]),
@@ -343,6 +345,47 @@ def hj_query_gradient(g: int, xs, ndim: int) -> np.ndarray:
     out = np.zeros_like(a)
     _check(lib().hj_query_gradient(g, a.shape[0], p, out.ctypes.data_as(_P(_d))))
     return out
+
+
+def hj_safety_filter(grids, axes, ctrl_index, states, u_perf, level: float = 0.0):
+    """Safety filter over decomposed subsystem grids (see hj.h).  grids:
+    Grid objects or handles; axes[k]: state index of each axis of grid k;
+    ctrl_index[k]: control driven by grid k (-1: none).  states (nq,
+    state_dim) and u_perf (nq, ctrl_dim): numpy (host) or float64 CUDA
+    tensors.  Returns (u, w, active) of the same kind."""
+    hs = [g.handle if hasattr(g, "handle") else g for g in grids]
+    k = len(hs)
+    ax = np.zeros((k, HJ_MAX_DIM), dtype=np.int32)
+    for i, a in enumerate(axes):
+        ax[i, :len(a)] = a
+    ci = np.ascontiguousarray(ctrl_index, dtype=np.int32)
+    harr = (_vp * k)(*hs)
+    try:
+        import torch
+        if isinstance(states, torch.Tensor):
+            nq, sd = states.shape
+            cd = u_perf.shape[1]
+            u = torch.empty_like(u_perf)
+            w = torch.empty(nq, dtype=torch.float64, device=states.device)
+            act = torch.empty(nq, dtype=torch.int32, device=states.device)
+            _check(lib().hj_safety_filter(harr, k, ax.ctypes.data_as(_P(_i)),
+                                          ci.ctypes.data_as(_P(_i)), sd, cd, nq,
+                                          states.data_ptr(), u_perf.data_ptr(), float(level),
+                                          u.data_ptr(), w.data_ptr(), act.data_ptr(), 1))
+            return u, w, act
+    except ImportError:  # pragma: no cover
+        pass
+    x = np.ascontiguousarray(states, dtype=np.float64)
+    up = np.ascontiguousarray(u_perf, dtype=np.float64)
+    nq, sd = x.shape
+    cd = up.shape[1]
+    u = np.empty_like(up)
+    w = np.empty(nq, dtype=np.float64)
+    act = np.empty(nq, dtype=np.int32)
+    _check(lib().hj_safety_filter(harr, k, ax.ctypes.data_as(_P(_i)), ci.ctypes.data_as(_P(_i)),
+                                  sd, cd, nq, x.ctypes.data, up.ctypes.data, float(level),
+                                  u.ctypes.data, w.ctypes.data, act.ctypes.data, 0))
+    return u, w, act
 
 
 def hj_autotune(g: int, scheme: int = HJ_WENO5) -> int:

@@ -11,6 +11,8 @@ solving, through the same C ABI:
   grid, and a warm fine solve.  The plain way is a cold fine solve.
 * local_wind_update (Sec. II-C, III-B): the wind bound rises near one
   place only; warm start from the previous result against a cold solve.
+* safety_filter (Sec. II-A, II-B): the decomposed 10-D filter, batch
+  throughput and single-state latency.
 * serving: a seeded request trace replayed through the continuous-batching
   server.  The plain way is one cold single-grid solve per request, in
   arrival order.
@@ -230,6 +232,45 @@ def local_wind_update(n4: int = 61, n2: int = 201, base: float = 0.5,
         g.close()
     speed = [r["cold_ms"] / r["warm_ms"] for r in rows]
     return dict(base=base, updates=rows, warm_speedup_p50=float(np.percentile(speed, 50)))
+
+
+def safety_filter(n4: int = 41, n2: int = 201, batch: int = 1 << 20, reps: int = 20,
+                  single: int = 200) -> Dict:
+    """The decomposed 10-D safety filter (Sec. II-A, II-B, III-A) over the x,
+    y (n4^4) and z (n2^2) subsystems of the 10-D demo: throughput for a batch
+    of states resident on the device, and the latency of one state through
+    host buffers, as a control loop would call it."""
+    import torch
+    specs = [wl.demo10d_x(n4, 0.5), wl.demo10d_x(n4, 0.5, "y"), wl.demo10d_z(n2, 0.5)]
+    grids = [hj.Grid.from_spec(s) for s in specs]
+    for g, s in zip(grids, specs):
+        g.solve(hj.HJ_COLD, **_opts_for(s))
+    states = wl.quad10d_states(specs, batch, seed=5)
+    up = np.tile([0.0, 0.0, 9.81 / 0.91], (batch, 1))
+    ts, tu = torch.from_numpy(states).cuda(), torch.from_numpy(up).cuda()
+    hj.hj_safety_filter(grids, wl.QUAD10D_AXES, wl.QUAD10D_CTRL, ts, tu, 0.0)
+    _sync()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        u, w, act = hj.hj_safety_filter(grids, wl.QUAD10D_AXES, wl.QUAD10D_CTRL, ts, tu, 0.0)
+    _sync()
+    dt_batch = (time.perf_counter() - t0) / reps
+    active = float((act != 0).float().mean().item())
+    one_x, one_u = states[:1].copy(), up[:1].copy()
+    hj.hj_safety_filter(grids, wl.QUAD10D_AXES, wl.QUAD10D_CTRL, one_x, one_u, 0.0)
+    lat = []
+    for i in range(single):
+        one_x[0] = states[i]
+        t1 = time.perf_counter()
+        hj.hj_safety_filter(grids, wl.QUAD10D_AXES, wl.QUAD10D_CTRL, one_x, one_u, 0.0)
+        lat.append(time.perf_counter() - t1)
+    for g in grids:
+        g.close()
+    return dict(grids=[s.name + "%s" % (s.n,) for s in specs], batch=batch,
+                batch_ms=1e3 * dt_batch, states_per_s=batch / dt_batch,
+                active_fraction=active,
+                single_state_us_p50=1e6 * float(np.percentile(lat, 50)),
+                single_state_us_p99=1e6 * float(np.percentile(lat, 99)))
 
 
 def load_reference(path: str) -> Optional[Dict]:

@@ -141,6 +141,27 @@ def two_band_margin(spec: ProblemSpec, bands: Sequence[Tuple[float, float]],
     return np.max([np.minimum(xs - lo, hi - xs) for lo, hi in bands], axis=0)
 
 
+# The 10-D near-hover quadcopter (Sec. IV): state (p_x, v_x, th_x, w_x, p_y,
+# v_y, th_y, w_y, p_z, v_z), inputs (u_x, u_y, T_z), decomposed into the x,
+# y and z subsystems.  State indices of each subsystem's axes, and the input
+# each subsystem drives.
+QUAD10D_AXES = ((0, 1, 2, 3), (4, 5, 6, 7), (8, 9))
+QUAD10D_CTRL = (0, 1, 2)
+
+
+def quad10d_states(specs: Sequence[ProblemSpec], count: int, seed: int = 7,
+                   inset: float = 0.02) -> np.ndarray:
+    """Seeded full 10-D states, uniform inside every subsystem grid box
+    (shrunk by `inset` of each axis length), for filter queries."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = np.zeros((count, 10))
+    for spec, axes in zip(specs, QUAD10D_AXES):
+        for d, a in enumerate(axes):
+            w = spec.hi[d] - spec.lo[d]
+            out[:, a] = rng.uniform(spec.lo[d] + inset * w, spec.hi[d] - inset * w, count)
+    return out
+
+
 # ---------------------------------------------------------------- configs
 
 def config0() -> ProblemSpec:

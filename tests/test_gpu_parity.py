@@ -191,6 +191,55 @@ def test_constraint_field_prolong_and_errors(hj):
     gf.close()
 
 
+def test_safety_filter_parity(hj):
+    """Decomposed 10-D safety filter (Sec. II-A, II-B, III-A) on the GPU
+    against the oracle's filter, on the same float32 value grids."""
+    specs = [wl.demo10d_x(15, 0.5), wl.demo10d_x(13, 0.7, "y"), wl.demo10d_z(61, 0.5)]
+    Ws = [oracle.solve(s, scheme=5 if s.ndim == 4 else 2, fixed_steps=40)[0].astype(np.float32)
+          for s in specs]
+    grids = []
+    for s, W in zip(specs, Ws):
+        g = hj.Grid.from_spec(s)
+        g.set_value(W)
+        grids.append(g)
+    states = wl.quad10d_states(specs, 20000, seed=11)
+    up = np.tile([0.05, -0.05, 9.0], (states.shape[0], 1))
+    W64 = [W.astype(np.float64) for W in Ws]
+    for level in (0.0, 0.3):
+        u, w, act = hj.hj_safety_filter(grids, wl.QUAD10D_AXES, wl.QUAD10D_CTRL, states, up, level)
+        uo, wo, ao = oracle.safety_filter(specs, W64, wl.QUAD10D_AXES, wl.QUAD10D_CTRL, states,
+                                          up, level)
+        assert np.abs(w - wo).max() <= 1e-9 * np.abs(wo).max()
+        # switching and bang-bang decisions are unique away from exact ties
+        vals = [oracle.query_value(s, W, states[:, list(a)])
+                for s, W, a in zip(specs, W64, wl.QUAD10D_AXES)]
+        grads = [oracle.query_gradient(s, W, states[:, list(a)])
+                 for s, W, a in zip(specs, W64, wl.QUAD10D_AXES)]
+        for k, s in enumerate(specs):
+            b, _, _ = oracle.control_gain(s)
+            gain = grads[k] @ b
+            clear = (np.abs(vals[k] - level) > 1e-9) & (np.abs(gain) > 1e-9)
+            assert np.array_equal(((act >> k) & 1)[clear], ((ao >> k) & 1)[clear])
+            assert np.array_equal(u[clear, k], uo[clear, k])
+        assert act.any() and (act == 0).any()
+    # device buffers on the grids' stream
+    import torch
+    ts, tu = torch.from_numpy(states).cuda(), torch.from_numpy(up).cuda()
+    ud, wd, ad = hj.hj_safety_filter(grids, wl.QUAD10D_AXES, wl.QUAD10D_CTRL, ts, tu, 0.0)
+    u0, w0, a0 = hj.hj_safety_filter(grids, wl.QUAD10D_AXES, wl.QUAD10D_CTRL, states, up, 0.0)
+    assert np.array_equal(ud.cpu().numpy(), u0) and np.array_equal(wd.cpu().numpy(), w0)
+    assert np.array_equal(ad.cpu().numpy(), a0)
+    # errors: a state outside a box, a control driven twice
+    bad = states[:4].copy()
+    bad[0, 0] = 100.0
+    with pytest.raises(hj.HJError):
+        hj.hj_safety_filter(grids, wl.QUAD10D_AXES, wl.QUAD10D_CTRL, bad, up[:4], 0.0)
+    with pytest.raises(hj.HJError):
+        hj.hj_safety_filter(grids, wl.QUAD10D_AXES, (0, 0, 2), states[:4], up[:4], 0.0)
+    for g in grids:
+        g.close()
+
+
 def test_monotone_clamp_parity(hj):
     spec = wl.quad_z(61, 0.8)
     dt = oracle.cfl_dt(spec)

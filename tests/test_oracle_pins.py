@@ -300,6 +300,49 @@ def test_constraint_field_equals_the_analytic_ball():
     assert np.array_equal(oracle.margin(s, l), l)
 
 
+def test_safety_control_brakes_toward_the_safe_set():
+    """The optimal safety control (Sec. II-A) on the z subsystem: near the
+    ceiling while climbing it cuts thrust to its lower bound; near the floor
+    while falling it applies full thrust (the braking curves of the double
+    integrator).  The x subsystem near its +p face moving outward commands
+    the lower input bound (tilt back), and the mirrored state the upper."""
+    z = wl.quad_z(61, 0.5)
+    Wz, st = oracle.solve(z, scheme=2, tol=1e-6, max_steps=50000)
+    assert st["converged"]
+    S = np.array([[2.3, 1.0], [0.7, -1.0]])
+    u, w, act = oracle.safety_filter([z], [Wz], [(0, 1)], [0], S, np.full((2, 1), 9.0),
+                                     level=10.0)
+    assert u[:, 0].tolist() == [wl.Z_PARAMS[2], wl.Z_PARAMS[3]]
+    assert act.tolist() == [1, 1]
+    x = wl.quad_x4(11, 0.5)
+    Wx, _ = oracle.solve(x, scheme=5, fixed_steps=200)
+    X = np.array([[3.6, 1.5, 0.0, 0.0], [-3.6, -1.5, 0.0, 0.0]])
+    u, w, act = oracle.safety_filter([x], [Wx], [(0, 1, 2, 3)], [0], X, np.zeros((2, 1)),
+                                     level=0.5)
+    assert u[:, 0].tolist() == [wl.X4_PARAMS[4], wl.X4_PARAMS[5]]
+
+
+def test_safety_filter_switch_and_decomposed_value():
+    """W = min over subsystems; the performance control passes where every
+    W_k is above the level; each subsystem drives only its own input."""
+    specs = [wl.demo10d_x(9, 0.5), wl.demo10d_x(9, 0.5, "y"), wl.demo10d_z(21, 0.5)]
+    Ws = [oracle.solve(s, scheme=2, fixed_steps=30)[0] for s in specs]
+    states = wl.quad10d_states(specs, 200, seed=3)
+    up = np.tile([0.1, -0.1, 9.0], (200, 1))
+    u, w, act = oracle.safety_filter(specs, Ws, wl.QUAD10D_AXES, wl.QUAD10D_CTRL, states, up,
+                                     level=-1e9)
+    assert np.array_equal(u, up) and not act.any()
+    vals = [oracle.query_value(s, W, states[:, list(a)])
+            for s, W, a in zip(specs, Ws, wl.QUAD10D_AXES)]
+    assert np.array_equal(w, np.minimum(np.minimum(vals[0], vals[1]), vals[2]))
+    u, w, act = oracle.safety_filter(specs, Ws, wl.QUAD10D_AXES, wl.QUAD10D_CTRL, states, up,
+                                     level=0.0)
+    for k in range(3):
+        on = (act >> k) & 1 == 1
+        assert np.array_equal(on, vals[k] <= 0.0)
+        assert np.array_equal(u[~on, k], up[~on, k])
+
+
 def test_uniform_field_equals_box():
     s = wl.quad_x4(9, 0.6)
     W0, _ = oracle.solve(s, scheme=5, fixed_steps=4)
