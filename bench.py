@@ -395,6 +395,7 @@ def main():
         scen = {"decomposed_update": scenarios.decomposed_update(),
                 "adaptive_grid": scenarios.adaptive_grid(reference=ref),
                 "local_wind_update": scenarios.local_wind_update(),
+                "moving_constraint": scenarios.moving_constraint(),
                 "safety_filter": scenarios.safety_filter(),
                 "serving": scenarios.serving(args.serve_requests)}
     if rank != 0:

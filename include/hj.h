@@ -188,6 +188,24 @@ hj_status hj_set_disturbance_bound(hj_grid g, const double* d_lo, const double* 
 hj_status hj_set_disturbance_field(hj_grid g, const float* d_lo, const float* d_hi, int nd,
                                    int on_device);
 
+/* Translated prior.  The quadcopter blocks' f does not depend on the
+ * position (axis 0), and a drift's on no axis, so when the constraint moves
+ * by `shift` along such axes the fixed point moves with it.  This writes
+ *   dst.W(x) = min(src.W(x - shift), l_dst(x))
+ * by multilinear interpolation of src's value; where x - shift leaves src's
+ * box, dst.W(x) = l_dst(x) (the cold start there).  The result is the prior
+ * of a following HJ_WARM solve of dst.
+ *   - src and dst are distinct grids with the same model and parameters; any
+ *     resolution and box.
+ *   - shift has ndim entries; it must be 0 on axes the dynamics depend on.
+ *   - Exact (up to the grid's truncation near its faces) when the shifted
+ *     constraint of src contains dst's and src's disturbance box lies in
+ *     dst's (Sec. III-B's dominance, modulo the translation).
+ * HJ_ERR_ARG on NULL, equal grids, other dynamics or a shift along a
+ * non-invariant axis; HJ_ERR_STATE without a source value or target
+ * constraint, or with a state-dependent disturbance bound on either. */
+hj_status hj_translate(hj_grid src, hj_grid dst, const double* shift);
+
 /* Iterate Eq. 2 to convergence.
  * Starting value:
  *   - HJ_COLD starts from l.
@@ -297,6 +315,9 @@ typedef struct {
   double p50_ms, p99_ms;        /* submit-to-completion latency of completed requests          */
   double updates;               /* grid-point updates (nodes x steps) of all finished requests */
   double busy_ms;               /* wall time from first submit to last completion              */
+  long long translated_starts;  /* warm starts from a translated prior (hj_translate): the key's */
+                                /* prior dominates once its constraint is moved along the       */
+                                /* position axis                                               */
 } hj_server_stats;
 
 /* Start a server on the current device.  hbm_budget_bytes bounds the device

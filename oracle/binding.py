@@ -239,6 +239,21 @@ def prolong(coarse, Wc: np.ndarray, fine, lfield_fine=None) -> np.ndarray:
     return Wf
 
 
+def translate(src, Ws: np.ndarray, dst, shift: Sequence[float], lfield_dst=None) -> np.ndarray:
+    """Translated prior: W_dst(x) = min(W_src(x - shift), l_dst(x)) by
+    multilinear interpolation; l_dst(x) where x - shift leaves src's box."""
+    Ws = np.ascontiguousarray(Ws, dtype=np.float64)
+    X = np.stack([a.ravel() for a in np.meshgrid(*dst.coords(), indexing="ij")], axis=1)
+    Y = X - np.asarray(shift, dtype=np.float64)[None, :]
+    t = (Y - np.asarray(src.lo)[None, :]) / np.asarray(src.h())[None, :]
+    inside = np.all((t >= -1e-9) & (t <= (np.asarray(src.n) - 1)[None, :] + 1e-9), axis=1)
+    l = margin(dst, lfield_dst).ravel()
+    out = l.copy()
+    if inside.any():
+        out[inside] = np.minimum(query_value(src, Ws, Y[inside]), l[inside])
+    return out.reshape(dst.n)
+
+
 def query_value(spec, W: np.ndarray, xs: np.ndarray) -> np.ndarray:
     W = np.ascontiguousarray(W, dtype=np.float64)
     xs = np.ascontiguousarray(xs, dtype=np.float64).reshape(-1, spec.ndim)
@@ -388,5 +403,6 @@ def z_closed_form(z: np.ndarray, v: np.ndarray, kT: float, g: float, u_hi: float
 
 __all__ = ["build", "lib", "solve", "alpha", "cfl_dt", "hamiltonian", "margin", "margin_at",
            "line_slopes", "rhs", "prolong", "query_value", "query_gradient", "brute_force_z",
-           "z_closed_form", "num_threads", "set_num_threads", "control_gain", "safety_filter"]
+           "z_closed_form", "num_threads", "set_num_threads", "control_gain", "safety_filter",
+           "translate"]
 

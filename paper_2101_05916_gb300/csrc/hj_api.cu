@@ -672,8 +672,33 @@ hj_status hj_solve(hj_grid g, int mode, const hj_solve_opts* o_in, hj_solve_stat
   return rc;
 }
 
+// dst.W = min(src.W(x - shift), l_dst); fill: source points outside the
+// source box give l_dst instead of an error.
+static hj_status migrate(hj_grid src, hj_grid dst, const double* shift, int fill) {
+  DeviceGuard dg(dst->device);
+  hjk::Shift sh;
+  std::memset(&sh, 0, sizeof(sh));
+  for (int i = 0; i < dst->ndim; ++i) sh.s[i] = shift ? shift[i] : 0.0;
+  sh.fill_outside = fill;
+  cudaEvent_t ev;
+  HJ_CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  cudaEventRecord(ev, src->stream);
+  cudaStreamWaitEvent(dst->stream, ev, 0);
+  cudaEventDestroy(ev);
+  HJ_CU(cudaMemsetAsync(dst->dscal + 5, 0, sizeof(unsigned), dst->stream));
+  HJ_CU(hjk::launch_prolong(devgrid(src), src->W, devgrid(dst), dst->W, sh,
+                            (int*)(dst->dscal + 5), dst->stream));
+  HJ_CU(cudaMemcpyAsync(dst->hscal + 5, dst->dscal + 5, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                        dst->stream));
+  HJ_CU(cudaStreamSynchronize(dst->stream));
+  if (dst->hscal[5]) return fail(HJ_ERR_ARG, "a fine node lies outside the coarse grid");
+  dst->has_value = true;
+  return HJ_OK;
+}
+
 hj_status hj_prolong(hj_grid coarse, hj_grid fine) {
   if (!coarse || !fine) return fail(HJ_ERR_ARG, "grid is NULL");
+  if (coarse == fine) return fail(HJ_ERR_ARG, "source and target are the same grid");
   if (coarse->ndim != fine->ndim) return fail(HJ_ERR_ARG, "grids differ in ndim");
   if (coarse->device != fine->device) return fail(HJ_ERR_ARG, "grids on different devices");
   if (!coarse->has_value) return fail(HJ_ERR_STATE, "coarse grid holds no value");
@@ -683,21 +708,32 @@ hj_status hj_prolong(hj_grid coarse, hj_grid fine) {
     if (fine->lo[i] < coarse->lo[i] - tol || fine->hi[i] > coarse->hi[i] + tol)
       return fail(HJ_ERR_ARG, "fine box leaves the coarse box on axis %d", i);
   }
-  DeviceGuard dg(fine->device);
-  cudaEvent_t ev;
-  HJ_CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-  cudaEventRecord(ev, coarse->stream);
-  cudaStreamWaitEvent(fine->stream, ev, 0);
-  cudaEventDestroy(ev);
-  HJ_CU(cudaMemsetAsync(fine->dscal + 5, 0, sizeof(unsigned), fine->stream));
-  HJ_CU(hjk::launch_prolong(devgrid(coarse), coarse->W, devgrid(fine), fine->W,
-                            (int*)(fine->dscal + 5), fine->stream));
-  HJ_CU(cudaMemcpyAsync(fine->hscal + 5, fine->dscal + 5, sizeof(unsigned), cudaMemcpyDeviceToHost,
-                        fine->stream));
-  HJ_CU(cudaStreamSynchronize(fine->stream));
-  if (fine->hscal[5]) return fail(HJ_ERR_ARG, "a fine node lies outside the coarse grid");
-  fine->has_value = true;
-  return HJ_OK;
+  return migrate(coarse, fine, nullptr, 0);
+}
+
+hj_status hj_translate(hj_grid src, hj_grid dst, const double* shift) {
+  if (!src || !dst || !shift) return fail(HJ_ERR_ARG, "NULL argument");
+  if (src == dst) return fail(HJ_ERR_ARG, "source and target are the same grid");
+  if (src->ndim != dst->ndim) return fail(HJ_ERR_ARG, "grids differ in ndim");
+  if (src->device != dst->device) return fail(HJ_ERR_ARG, "grids on different devices");
+  if (!src->has_value) return fail(HJ_ERR_STATE, "source grid holds no value");
+  if (dst->con_kind < 0) return fail(HJ_ERR_STATE, "target grid has no constraint");
+  if (src->model != dst->model || src->model < 0)
+    return fail(HJ_ERR_ARG, "source and target have different dynamics");
+  for (int i = 0; i < 8; ++i)
+    if (src->params[i] != dst->params[i])
+      return fail(HJ_ERR_ARG, "source and target have different model parameters");
+  if (src->dfield_nd > 0 || dst->dfield_nd > 0)
+    return fail(HJ_ERR_STATE, "a state-dependent disturbance bound is not translation invariant");
+  for (int i = 0; i < dst->ndim; ++i) {
+    if (!std::isfinite(shift[i])) return fail(HJ_ERR_ARG, "shift must be finite");
+    // f depends on every axis but the position (axis 0) for the quadcopter
+    // blocks, on none for the drift
+    bool invariant = dst->model == HJ_DRIFT || i == 0;
+    if (shift[i] != 0.0 && !invariant)
+      return fail(HJ_ERR_ARG, "the dynamics are not invariant along axis %d", i);
+  }
+  return migrate(src, dst, shift, 1);
 }
 
 hj_status hj_set_value(hj_grid g, const float* src, int on_device) {

@@ -24,10 +24,16 @@ cudaError_t launch_stage(const hjd::DevGrid& g, int scheme, int stage, const hjd
 cudaError_t launch_alpha(const hjd::DevGrid& g, unsigned* out, cudaStream_t s);
 // W = l (warm = 0) or W = min(W, l) (warm = 1); snap = W.
 cudaError_t launch_init(const hjd::DevGrid& g, float* W, float* snap, int warm, cudaStream_t s);
-// Wf = min(multilinear(Wc) at fine nodes, l_fine); *bad = 1 if a fine node lies
-// outside the coarse box.
+// Offset of a migration: the target node x reads the source at x - s.
+struct Shift {
+  double s[4];
+  int fill_outside;  // 1: a node whose source point leaves the source box gets l
+};
+// Wf = min(multilinear(Wc) at x - shift for every target node x, l_target).
+// A source point outside the source box sets *bad = 1, or with fill_outside
+// gives the node l_target.
 cudaError_t launch_prolong(const hjd::DevGrid& c, const float* Wc, const hjd::DevGrid& f,
-                           float* Wf, int* bad, cudaStream_t s);
+                           float* Wf, const Shift& sh, int* bad, cudaStream_t s);
 // Multilinear value (grad = 0) or node-gradient interpolation (grad = 1) at npts
 // points x (device, point-major doubles).  *bad is set to 1 when a point lies
 // outside the box.

@@ -90,7 +90,7 @@ __global__ void init_kernel(const DevGrid g, float* W, float* snap, int warm) {
 
 template <int D>
 __global__ void prolong_kernel(const DevGrid c, const float* __restrict__ Wc, const DevGrid f,
-                               float* Wf, int* bad) {
+                               float* Wf, hjk::Shift sh, int* bad) {
   for (int pt = blockIdx.x * blockDim.x + threadIdx.x; pt < f.npts; pt += gridDim.x * blockDim.x) {
     int idx[D];
     unravel<D>(f, pt, idx);
@@ -102,10 +102,13 @@ __global__ void prolong_kernel(const DevGrid c, const float* __restrict__ Wc, co
     for (int d = 0; d < D; ++d) {
       double xv = f.lo_d[d] + (double)idx[d] * f.h_d[d];
       xf[d] = (float)xv;
-      ok = ok && locate(c, d, xv, i0[d], fr[d]);
+      ok = ok && locate(c, d, xv - sh.s[d], i0[d], fr[d]);
     }
+    float l = hjd::margin<D>(f, xf, pt);
     if (!ok) {
-      *bad = 1;
+      // outside the source box: the cold start there, or an error
+      if (sh.fill_outside) Wf[pt] = l;
+      else *bad = 1;
       continue;
     }
     double acc = 0.0;
@@ -121,7 +124,7 @@ __global__ void prolong_kernel(const DevGrid c, const float* __restrict__ Wc, co
       }
       acc += wgt * (double)__ldg(Wc + off);
     }
-    Wf[pt] = fminf((float)acc, hjd::margin<D>(f, xf, pt));
+    Wf[pt] = fminf((float)acc, l);
   }
 }
 
@@ -273,13 +276,13 @@ cudaError_t launch_init(const DevGrid& g, float* W, float* snap, int warm, cudaS
 }
 
 cudaError_t launch_prolong(const DevGrid& c, const float* Wc, const DevGrid& f, float* Wf,
-                           int* bad, cudaStream_t s) {
+                           const Shift& sh, int* bad, cudaStream_t s) {
   unsigned nb = flat_blocks(f.npts, 256);
   switch (f.ndim) {
-    case 1: prolong_kernel<1><<<nb, 256, 0, s>>>(c, Wc, f, Wf, bad); break;
-    case 2: prolong_kernel<2><<<nb, 256, 0, s>>>(c, Wc, f, Wf, bad); break;
-    case 3: prolong_kernel<3><<<nb, 256, 0, s>>>(c, Wc, f, Wf, bad); break;
-    case 4: prolong_kernel<4><<<nb, 256, 0, s>>>(c, Wc, f, Wf, bad); break;
+    case 1: prolong_kernel<1><<<nb, 256, 0, s>>>(c, Wc, f, Wf, sh, bad); break;
+    case 2: prolong_kernel<2><<<nb, 256, 0, s>>>(c, Wc, f, Wf, sh, bad); break;
+    case 3: prolong_kernel<3><<<nb, 256, 0, s>>>(c, Wc, f, Wf, sh, bad); break;
+    case 4: prolong_kernel<4><<<nb, 256, 0, s>>>(c, Wc, f, Wf, sh, bad); break;
     default: return cudaErrorInvalidValue;
   }
   g_launches.fetch_add(1, std::memory_order_relaxed);

@@ -93,6 +93,37 @@ bool dominates(const hj_request& prior, const hj_request& req) {
   return true;
 }
 
+// Dominance modulo a translation (hj_translate): along axes the dynamics do
+// not depend on (the position axis of the quadcopter blocks, every axis of a
+// drift) the prior's constraint may be moved by *shift; it must then contain
+// the new one.  The shift centres the prior's box on the new one.  False when
+// no translation is needed (plain dominance covers that).
+bool dominates_translated(const hj_request& prior, const hj_request& req, double* shift) {
+  if (!same_geometry(prior, req) || prior.nd != req.nd) return false;
+  for (int i = 0; i < req.nd; ++i)
+    if (prior.d_lo[i] < req.d_lo[i] || prior.d_hi[i] > req.d_hi[i]) return false;
+  if (prior.con_ball != req.con_ball) return false;
+  bool moved = false;
+  for (int i = 0; i < req.ndim; ++i) {
+    shift[i] = 0.0;
+    bool invariant = req.model == HJ_DRIFT || i == 0;
+    double pa = prior.con_a[i], pb = prior.con_b[i], ra = req.con_a[i], rb = req.con_b[i];
+    if (!req.con_ball) {
+      if (invariant && std::isfinite(pa) && std::isfinite(pb) && std::isfinite(ra) &&
+          std::isfinite(rb))
+        shift[i] = 0.5 * ((ra + rb) - (pa + pb));
+      double tol = 1e-9 * (1.0 + std::fabs(ra) + std::fabs(rb));
+      if (pa + shift[i] > ra + tol || pb + shift[i] < rb - tol) return false;
+    } else {
+      if (invariant) shift[i] = ra - pa;
+      else if (pa != ra) return false;
+    }
+    moved = moved || shift[i] != 0.0;
+  }
+  if (req.con_ball && prior.con_b[0] > req.con_b[0]) return false;
+  return moved;
+}
+
 hj_status make_grid(const hj_request& r, cudaStream_t s, hj_grid* out) {
   hj_grid g = nullptr;
   hj_status st = hj_grid_create(&g, r.ndim, r.n, r.lo, r.hi, s);
@@ -250,6 +281,7 @@ void hj_server_s::admit_locked(std::vector<long long>& admitted) {
       auto rk = resident_of_key.find(q.r.key);
       if (rk != resident_of_key.end()) {
         Req& p = reqs[rk->second];
+        double shift[HJ_MAX_DIM];
         if (p.g && dominates(p.r, q.r)) {
           cudaError_t e = cudaMemcpyAsync(g->W, p.g->W, (size_t)q.npts * sizeof(float),
                                           cudaMemcpyDeviceToDevice, stream);
@@ -257,6 +289,12 @@ void hj_server_s::admit_locked(std::vector<long long>& admitted) {
           if (e == cudaSuccess) {
             g->has_value = true;
             mode = HJ_WARM;
+            p.last_use = Clock::now();
+          }
+        } else if (p.g && dominates_translated(p.r, q.r, shift)) {
+          if (hj_translate(p.g, g, shift) == HJ_OK) {
+            mode = HJ_WARM;
+            st.translated_starts++;
             p.last_use = Clock::now();
           }
         }

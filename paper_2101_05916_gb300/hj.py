@@ -77,7 +77,7 @@ class hj_server_stats(ctypes.Structure):
                 ("rejected", _ll), ("warm_starts", _ll), ("cold_starts", _ll),
                 ("evictions", _ll), ("rounds", _ll), ("bytes_in_use", _ll),
                 ("peak_bytes", _ll), ("active", _ll), ("queued", _ll), ("p50_ms", _d),
-                ("p99_ms", _d), ("updates", _d), ("busy_ms", _d)]
+                ("p99_ms", _d), ("updates", _d), ("busy_ms", _d), ("translated_starts", _ll)]
 
     def as_dict(self) -> Dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -98,6 +98,7 @@ SIGNATURES = {
     "hj_solve_batch": (_i, [_P(_vp), _i, _P(_i), _P(hj_solve_opts), _i, _P(hj_solve_stats),
                             _P(_i)]),
     "hj_prolong": (_i, [_vp, _vp]),
+    "hj_translate": (_i, [_vp, _vp, _P(_d)]),
     "hj_set_value": (_i, [_vp, _vp, _i]),
     "hj_get_value": (_i, [_vp, _vp, _i]),
     "hj_query_value": (_i, [_vp, _i, _P(_d), _P(_d)]),
@@ -598,6 +599,14 @@ def solve_batch(grids: List[Grid], modes: Sequence[int], **kw):
 
 def prolong(coarse: Grid, fine: Grid) -> None:
     hj_prolong(coarse.handle, fine.handle)
+
+
+def hj_translate(src: int, dst: int, shift: Sequence[float]) -> None:
+    _check(lib().hj_translate(src, dst, _darr(shift)))
+
+
+def translate(src: Grid, dst: Grid, shift: Sequence[float]) -> None:
+    hj_translate(src.handle, dst.handle, shift)
 
 
 def cfl_steps(check_dt: float, dt: float) -> int:

@@ -11,6 +11,8 @@ solving, through the same C ABI:
   grid, and a warm fine solve.  The plain way is a cold fine solve.
 * local_wind_update (Sec. II-C, III-B): the wind bound rises near one
   place only; warm start from the previous result against a cold solve.
+* moving_constraint: the box moves along the position axis; warm start from
+  the translated prior against a cold solve.
 * safety_filter (Sec. II-A, II-B): the decomposed 10-D filter, batch
   throughput and single-state latency.
 * serving: a seeded request trace replayed through the continuous-batching
@@ -232,6 +234,56 @@ def local_wind_update(n4: int = 61, n2: int = 201, base: float = 0.5,
         g.close()
     speed = [r["cold_ms"] / r["warm_ms"] for r in rows]
     return dict(base=base, updates=rows, warm_speedup_p50=float(np.percentile(speed, 50)))
+
+
+def moving_constraint(n4: int = 61, n2: int = 201, b: float = 0.5,
+                      shifts: Sequence[float] = (0.25, 0.5, 0.25, -0.25)) -> Dict:
+    """The constraint box moves along the position axis (a moving safe
+    corridor).  The quadcopter blocks' dynamics do not depend on position,
+    so each update warm-starts from the previous fixed point translated by
+    the move (hj_translate); the plain way is a cold solve of the moved box.
+    x (n4^4) boxes |p - s| <= 4 on [-5, 5]; z (n2^2) boxes [0.5, 2.5] + s/2."""
+    rows = []
+    for kind in ("x", "z"):
+        def spec_at(sh):
+            if kind == "x":
+                return wl.quad_x4(n4, b, shift=sh)
+            return wl.quad_z(n2, b, (0.5 + 0.5 * sh, 2.5 + 0.5 * sh))
+        prev_shift = 0.0
+        prev = hj.Grid.from_spec(spec_at(0.0))
+        opts = hj.make_opts(**_opts_for(prev.spec))
+        hj.hj_solve(prev.handle, hj.HJ_COLD, opts, raise_on_error=False)
+        for sh in shifts:
+            spec = spec_at(sh)
+            move = (sh - prev_shift) * (1.0 if kind == "x" else 0.5)
+            cur = hj.Grid.from_spec(spec)
+            _sync()
+            t0 = time.perf_counter()
+            hj.translate(prev, cur, [move] + [0.0] * (spec.ndim - 1))
+            rcw, stw = hj.hj_solve(cur.handle, hj.HJ_WARM, opts, raise_on_error=False)
+            _sync()
+            t1 = time.perf_counter()
+            Ww = cur.value()
+            cold = hj.Grid.from_spec(spec)
+            _sync()
+            t2 = time.perf_counter()
+            rcc, stc = hj.hj_solve(cold.handle, hj.HJ_COLD, opts, raise_on_error=False)
+            _sync()
+            t3 = time.perf_counter()
+            Wc = cold.value()
+            cold.close()
+            rows.append(dict(grid=spec.name + "%s" % (spec.n,), move=move,
+                             translated_warm_ms=1e3 * (t1 - t0), warm_steps=stw["steps"],
+                             cold_ms=1e3 * (t3 - t2), cold_steps=stc["steps"],
+                             statuses=[int(rcw), int(rcc)],
+                             sign_agreement=float(np.mean((Ww >= 0) == (Wc >= 0))),
+                             max_abs_diff_in_band=float(
+                                 np.abs(Ww - Wc)[np.abs(Wc) <= 0.5].max())))
+            prev.close()
+            prev, prev_shift = cur, sh
+        prev.close()
+    speed = [r["cold_ms"] / r["translated_warm_ms"] for r in rows]
+    return dict(updates=rows, speedup_p50=float(np.percentile(speed, 50)))
 
 
 def safety_filter(n4: int = 41, n2: int = 201, batch: int = 1 << 20, reps: int = 20,

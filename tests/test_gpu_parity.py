@@ -240,6 +240,54 @@ def test_safety_filter_parity(hj):
         g.close()
 
 
+def test_translate_parity_and_errors(hj):
+    """hj_translate against the oracle: non-aligned shifts along the position
+    axis, resolution change, and nodes whose source leaves the box."""
+    cases = [(wl.quad_z(41, 0.5, (0.5, 2.5)), wl.quad_z(67, 0.7, (0.83, 2.83)), (0.33, 0.0)),
+             (wl.quad_x4(13, 0.5), wl.quad_x4(15, 0.5, shift=-0.7), (-0.7, 0.0, 0.0, 0.0))]
+    for src, dst, shift in cases:
+        Ws = (oracle.margin(src) + wl.seeded_field(src, 3, 0.05)).astype(np.float32)
+        gs, gd = hj.Grid.from_spec(src), hj.Grid.from_spec(dst)
+        gs.set_value(Ws)
+        hj.translate(gs, gd, shift)
+        Wo = oracle.translate(src, Ws.astype(np.float64), dst, shift)
+        assert np.abs(gd.value() - Wo).max() <= 1e-6 * np.abs(Wo).max()
+        bad_shift = list(shift)
+        bad_shift[1] = 0.1
+        with pytest.raises(hj.HJError):
+            hj.translate(gs, gd, bad_shift)
+        with pytest.raises(hj.HJError):
+            hj.translate(gs, gs, shift)
+        gs.close()
+        gd.close()
+    # a state-dependent disturbance bound breaks translation invariance
+    z = wl.quad_z(21, 0.5)
+    g1, g2 = hj.Grid.from_spec(z), hj.Grid.from_spec(z)
+    g1.solve(hj.HJ_COLD, scheme=2, fixed_steps=2)
+    g2.set_disturbance_field(*wl.wind_field(z, 0.5, 0.2, 0, 1.0, 0.5))
+    with pytest.raises(hj.HJError) as e:
+        hj.translate(g1, g2, (0.1, 0.0))
+    assert e.value.status == hj.HJ_ERR_STATE
+    g1.close()
+    g2.close()
+
+
+def test_translated_warm_start_reaches_cold_fixed_point(hj):
+    z0 = wl.quad_z(101, 0.5, (0.5, 2.5))
+    z1 = wl.quad_z(101, 0.5, (0.65, 2.65))
+    g0, g1 = hj.Grid.from_spec(z0), hj.Grid.from_spec(z1)
+    g0.solve(hj.HJ_COLD, scheme=2, tol=1e-5)
+    hj.translate(g0, g1, (0.15, 0.0))
+    warm = g1.solve(hj.HJ_WARM, scheme=2, tol=1e-5)
+    Ww = g1.value()
+    cold = g1.solve(hj.HJ_COLD, scheme=2, tol=1e-5)
+    Wc = g1.value()
+    g0.close()
+    g1.close()
+    assert warm["converged"] and cold["converged"] and warm["steps"] < cold["steps"]
+    assert np.abs(Ww - Wc).max() <= 1e-4 * np.abs(Wc).max()
+
+
 def test_monotone_clamp_parity(hj):
     spec = wl.quad_z(61, 0.8)
     dt = oracle.cfl_dt(spec)

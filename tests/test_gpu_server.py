@@ -241,3 +241,30 @@ def test_coarse_initialisation_in_the_server(hj):
             hj.hj_server_submit(s2, hj.make_request(spec, 0, 0, coarse_n=2, **opts))
         finally:
             hj.hj_server_destroy(s2)
+
+
+def test_translated_prior_warm_start(hj):
+    """A key's resident prior whose constraint box, moved along the position
+    axis, equals the new one warm-starts the request through hj_translate and
+    reaches the cold fixed point; a moved box with a smaller wind bound does
+    not dominate and starts cold."""
+    s = hj.hj_server_create(4 << 30, 8)
+    key = 91
+    first = wl.quad_z(101, 0.5, (0.5, 2.5))
+    rc, st0, _ = fetch(hj, s, run(hj, s, first, 2, 0.0, hj.HJ_WARM, key, tol=1e-5), first)
+    moved = wl.quad_z(101, 0.6, (0.65, 2.65))
+    rc, st1, W = fetch(hj, s, run(hj, s, moved, 2, 0.0, hj.HJ_WARM, key, tol=1e-5), moved)
+    stats = hj.hj_server_get_stats(s)
+    weaker = wl.quad_z(101, 0.3, (0.4, 2.4))
+    rc2, _, _ = fetch(hj, s, run(hj, s, weaker, 2, 0.0, hj.HJ_WARM, key, tol=1e-5), weaker)
+    stats2 = hj.hj_server_get_stats(s)
+    hj.hj_server_destroy(s)
+    assert rc == hj.HJ_OK and rc2 == hj.HJ_OK
+    assert stats["translated_starts"] == 1 and stats["warm_starts"] == 1
+    assert stats2["translated_starts"] == 1 and stats2["cold_starts"] == 2
+    g = hj.Grid.from_spec(moved)
+    stc = g.solve(hj.HJ_COLD, scheme=2, tol=1e-5)
+    Wc = g.value()
+    g.close()
+    assert st1["steps"] < stc["steps"]
+    assert np.abs(W - Wc).max() <= REL * np.abs(Wc).max()

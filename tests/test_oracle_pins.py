@@ -343,6 +343,40 @@ def test_safety_filter_switch_and_decomposed_value():
         assert np.array_equal(u[~on, k], up[~on, k])
 
 
+def test_translation_on_the_grid_is_an_index_shift():
+    """A shift by whole cells moves the node values by whole indices; nodes
+    whose source leaves the box take the cold start l."""
+    z0 = wl.quad_z(61, 0.5, (0.5, 2.5))
+    z1 = wl.quad_z(61, 0.5, (0.7, 2.7))
+    W0 = oracle.margin(z0) + wl.seeded_field(z0, 5, 0.05)
+    l1 = oracle.margin(z1)
+    for k in (4, -3):
+        shift = (k * z0.h()[0], 0.0)
+        P = oracle.translate(z0, W0, z1, shift)
+        moved = np.full_like(W0, np.inf)
+        if k > 0:
+            moved[k:] = W0[:-k]
+        else:
+            moved[:k] = W0[-k:]
+        ref = np.minimum(np.where(np.isinf(moved), l1, moved), l1)
+        assert np.abs(P - ref).max() < 1e-12
+
+
+def test_translated_prior_warm_start_is_exact():
+    """The z dynamics do not depend on z, so the fixed point for a box moved
+    along z is the moved fixed point: a warm start from the translated prior
+    lands on the cold fixed point, in fewer steps (Sec. III-B)."""
+    z0 = wl.quad_z(61, 0.5, (0.5, 2.5))
+    z1 = wl.quad_z(61, 0.5, (0.7, 2.7))
+    W0, _ = oracle.solve(z0, scheme=2, tol=1e-6, max_steps=50000)
+    P = oracle.translate(z0, W0, z1, (0.2, 0.0))
+    Wc, stc = oracle.solve(z1, scheme=2, tol=1e-6, max_steps=50000)
+    Ww, stw = oracle.solve(z1, scheme=2, tol=1e-6, max_steps=50000, warm=P)
+    assert stc["converged"] and stw["converged"]
+    assert stw["steps"] < stc["steps"]
+    assert np.abs(Ww - Wc).max() < 1e-5
+
+
 def test_uniform_field_equals_box():
     s = wl.quad_x4(9, 0.6)
     W0, _ = oracle.solve(s, scheme=5, fixed_steps=4)
