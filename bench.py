@@ -411,6 +411,8 @@ def main():
         latency.update({"served_p50": sv["served"]["p50_ms"], "served_p99": sv["served"]["p99_ms"],
                         "served_coarse_init_p50": sv["served_coarse_init"]["p50_ms"],
                         "served_coarse_init_p99": sv["served_coarse_init"]["p99_ms"],
+                        "served_coarse_init_eno2_p50": sv["served_coarse_init_eno2"]["p50_ms"],
+                        "served_coarse_init_eno2_p99": sv["served_coarse_init_eno2"]["p99_ms"],
                         "plain_cold_p50": sv["plain_cold"]["p50_ms"],
                         "plain_cold_p99": sv["plain_cold"]["p99_ms"],
                         "serving_requests": sv["requests"]})

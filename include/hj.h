@@ -304,6 +304,11 @@ typedef struct {
                                 /* box, then migrates that value to its own grid (hj_prolong)   */
                                 /* and finishes with a warm solve there.  Exact or conservative */
                                 /* (Sec. III-B), usually far fewer fine steps.  0: off.         */
+  int coarse_n2;                /* > coarse_n: an intermediate level (coarse -> coarse_n2 ->   */
+                                /* n, each migrated and warm-solved; more levels "refined over */
+                                /* time", Sec. III-C).  0: none.  Needs coarse_n.              */
+  int coarse_scheme;            /* scheme of the coarse levels (cheap gradients on the coarse  */
+                                /* grid, e.g. HJ_ENO2: faster, more conservative); 0: opts'    */
 } hj_request;
 
 typedef struct {

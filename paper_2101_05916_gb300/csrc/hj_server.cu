@@ -41,12 +41,16 @@ enum ReqState { Q_QUEUED = 0, Q_RUNNING = 1, Q_DONE = 2 };
 struct Req {
   long long ticket = 0;
   hj_request r{};
-  size_t bytes = 0;          // fine grid bytes (plus the coarse grid while it lives)
-  size_t coarse_bytes = 0;
+  size_t bytes = 0;          // fine grid bytes (plus the coarse grids while they live)
+  size_t coarse_bytes = 0;   // current coarse level
   long long npts = 0;
-  long long coarse_npts = 0;
+  long long coarse_npts = 0; // current coarse level
   int phase = 0;             // 0: single solve; 1: coarse phase; 2: fine phase after migration
-  hj_grid gc = nullptr;      // coarse grid of the coarse phase
+  hj_grid gc = nullptr;      // grid of the current coarse level
+  int nlev = 0, lev = 0;     // coarse levels, and the one stepping now
+  int lev_n[2] = {0, 0};     // nodes per axis of each coarse level
+  long long lev_npts[2] = {0, 0};
+  size_t lev_bytes[2] = {0, 0};
   long long coarse_steps = 0;
   Clock::time_point t_submit, t_done;
   int state = Q_QUEUED;
@@ -122,6 +126,13 @@ bool dominates_translated(const hj_request& prior, const hj_request& req, double
   }
   if (req.con_ball && prior.con_b[0] > req.con_b[0]) return false;
   return moved;
+}
+
+// Solve options of the coarse levels: the request's, with its coarse scheme.
+hj_solve_opts coarse_opts(const hj_request& r) {
+  hj_solve_opts o = r.opts;
+  if (r.coarse_scheme) o.scheme = r.coarse_scheme;
+  return o;
 }
 
 hj_status make_grid(const hj_request& r, cudaStream_t s, hj_grid* out) {
@@ -248,10 +259,10 @@ void hj_server_s::admit_locked(std::vector<long long>& admitted) {
       // coarse initialisation: the coarse grid steps first; the fine grid
       // waits for the migrated value
       hj_request rc = q.r;
-      for (int i = 0; i < rc.ndim; ++i) rc.n[i] = rc.coarse_n;
+      for (int i = 0; i < rc.ndim; ++i) rc.n[i] = q.lev_n[0];
       s = make_grid(rc, stream, &q.gc);
       int slot = -1;
-      if (s == HJ_OK) s = runner->add(q.gc, HJ_COLD, q.r.opts, &slot);
+      if (s == HJ_OK) s = runner->add(q.gc, HJ_COLD, coarse_opts(q.r), &slot);
       if (s != HJ_OK) {
         if (q.gc) hj_grid_destroy(q.gc);
         q.gc = nullptr;
@@ -355,16 +366,49 @@ void hj_server_s::run() {
         // coarse phase done: migrate to the fine grid and step it from there
         hj_solve_stats cs{};
         hj_status r = runner->collect(q.slot, &cs);
-        q.coarse_steps = cs.steps;
-        int slot = -1;
-        if (r == HJ_OK || r == HJ_ERR_NOT_CONVERGED) r = hj_prolong(q.gc, q.g);
-        if (r == HJ_OK) r = runner->add(q.g, HJ_WARM, q.r.opts, &slot);
-        hj_grid_destroy(q.gc);
-        q.gc = nullptr;
-        used -= q.coarse_bytes;
-        q.bytes -= q.coarse_bytes;
-        active_nodes -= q.coarse_npts;
+        q.coarse_steps += cs.steps;
         st.updates += (double)q.coarse_npts * (double)cs.steps;
+        int slot = -1;
+        if (q.lev + 1 < q.nlev) {
+          // next coarse level: migrate up one level and step it warm
+          hj_request rn = q.r;
+          for (int i = 0; i < rn.ndim; ++i) rn.n[i] = q.lev_n[q.lev + 1];
+          hj_grid gn = nullptr;
+          if (r == HJ_OK || r == HJ_ERR_NOT_CONVERGED) r = make_grid(rn, stream, &gn);
+          if (r == HJ_OK) r = hj_prolong(q.gc, gn);
+          if (r == HJ_OK) r = runner->add(gn, HJ_WARM, coarse_opts(q.r), &slot);
+          hj_grid_destroy(q.gc);
+          q.gc = nullptr;
+          used -= q.coarse_bytes;
+          q.bytes -= q.coarse_bytes;
+          active_nodes -= q.coarse_npts;
+          if (r == HJ_OK) {
+            q.lev++;
+            q.gc = gn;
+            q.slot = slot;
+            q.coarse_npts = q.lev_npts[q.lev];
+            q.coarse_bytes = q.lev_bytes[q.lev];
+            active_nodes += q.coarse_npts;
+            ++it;
+            continue;
+          }
+          if (gn) hj_grid_destroy(gn);
+          // the remaining coarse level's reservation goes with the failure
+          used -= q.lev_bytes[q.lev + 1];
+          q.bytes -= q.lev_bytes[q.lev + 1];
+          q.coarse_npts = 0;
+          q.coarse_bytes = 0;
+        } else {
+          if (r == HJ_OK || r == HJ_ERR_NOT_CONVERGED) r = hj_prolong(q.gc, q.g);
+          if (r == HJ_OK) r = runner->add(q.g, HJ_WARM, q.r.opts, &slot);
+          hj_grid_destroy(q.gc);
+          q.gc = nullptr;
+          used -= q.coarse_bytes;
+          q.bytes -= q.coarse_bytes;
+          active_nodes -= q.coarse_npts;
+          q.coarse_npts = 0;
+          q.coarse_bytes = 0;
+        }
         if (r == HJ_OK) {
           q.slot = slot;
           q.phase = 2;
@@ -396,8 +440,11 @@ void hj_server_s::run() {
         if (q.gc) {
           hj_grid_destroy(q.gc);
           q.gc = nullptr;
-          used -= q.coarse_bytes;
-          q.bytes -= q.coarse_bytes;
+          // this level and any level not reached yet
+          size_t left = 0;
+          for (int l = q.lev; l < q.nlev; ++l) left += q.lev_bytes[l];
+          used -= left;
+          q.bytes -= left;
         }
         latencies.push_back(s.wall_ms);
         // grid-point updates count for every request that stepped, converged or not
@@ -496,16 +543,31 @@ hj_status hj_server_submit(hj_server s, const hj_request* r, long long* ticket) 
     if (npts >= (1ll << 31)) return hja::fail(HJ_ERR_ARG, "grid too large");
   }
   if (r->mode != HJ_COLD && r->mode != HJ_WARM) return hja::fail(HJ_ERR_ARG, "bad mode");
-  long long cnpts = 0;
+  int lev_n[2] = {0, 0};
+  int nlev = 0;
   if (r->coarse_n != 0) {
     if (r->coarse_n < 3) return hja::fail(HJ_ERR_ARG, "coarse_n must be 0 or >= 3");
-    cnpts = 1;
-    for (int i = 0; i < r->ndim; ++i) {
-      if (r->coarse_n > r->n[i]) return hja::fail(HJ_ERR_ARG, "coarse_n exceeds axis %d", i);
-      cnpts *= r->coarse_n;
-    }
+    lev_n[nlev++] = r->coarse_n;
   }
-  size_t cbytes = cnpts ? grid_bytes(cnpts) : 0;
+  if (r->coarse_n2 != 0) {
+    if (!r->coarse_n || r->coarse_n2 <= r->coarse_n)
+      return hja::fail(HJ_ERR_ARG, "coarse_n2 needs coarse_n < coarse_n2");
+    lev_n[nlev++] = r->coarse_n2;
+  }
+  if (r->coarse_scheme != 0 && r->coarse_scheme != HJ_FIRST &&
+      r->coarse_scheme != HJ_ENO2 && r->coarse_scheme != HJ_WENO5)
+    return hja::fail(HJ_ERR_ARG, "bad coarse_scheme");
+  long long lev_npts[2] = {0, 0};
+  size_t lev_bytes[2] = {0, 0};
+  for (int l = 0; l < nlev; ++l) {
+    lev_npts[l] = 1;
+    for (int i = 0; i < r->ndim; ++i) {
+      if (lev_n[l] > r->n[i]) return hja::fail(HJ_ERR_ARG, "coarse level exceeds axis %d", i);
+      lev_npts[l] *= lev_n[l];
+    }
+    lev_bytes[l] = grid_bytes(lev_npts[l]);
+  }
+  size_t cbytes = lev_bytes[0] + lev_bytes[1];
   size_t bytes = grid_bytes(npts) + cbytes;
   std::lock_guard<std::mutex> lk(s->mu);
   if (bytes > s->budget) {
@@ -516,9 +578,15 @@ hj_status hj_server_submit(hj_server s, const hj_request* r, long long* ticket) 
   q.ticket = s->next_ticket++;
   q.r = *r;
   q.bytes = bytes;
-  q.coarse_bytes = cbytes;
+  q.nlev = nlev;
+  for (int l = 0; l < 2; ++l) {
+    q.lev_n[l] = lev_n[l];
+    q.lev_npts[l] = lev_npts[l];
+    q.lev_bytes[l] = lev_bytes[l];
+  }
+  q.coarse_bytes = lev_bytes[0];
   q.npts = npts;
-  q.coarse_npts = cnpts;
+  q.coarse_npts = lev_npts[0];
   q.t_submit = Clock::now();
   q.last_use = q.t_submit;
   if (!s->first_submit_seen) {

@@ -69,7 +69,8 @@ class hj_request(ctypes.Structure):
                 ("hi", _d * HJ_MAX_DIM), ("model", _i), ("params", _d * 8), ("nparams", _i),
                 ("d_lo", _d * HJ_MAX_DIM), ("d_hi", _d * HJ_MAX_DIM), ("nd", _i),
                 ("con_ball", _i), ("con_a", _d * HJ_MAX_DIM), ("con_b", _d * HJ_MAX_DIM),
-                ("mode", _i), ("key", _ll), ("opts", hj_solve_opts), ("coarse_n", _i)]
+                ("mode", _i), ("key", _ll), ("opts", hj_solve_opts), ("coarse_n", _i),
+                ("coarse_n2", _i), ("coarse_scheme", _i)]
 
 
 class hj_server_stats(ctypes.Structure):
@@ -423,10 +424,14 @@ def hj_solve_fixed_static(spec, W, mode: int = HJ_COLD, scheme: int = HJ_WENO5,
 
 
 def make_request(spec, mode: int = HJ_COLD, key: int = 0, coarse_n: int = 0,
-                 **opts) -> hj_request:
-    """An hj_request for a workloads.ProblemSpec (coarse_n > 0: coarse initialisation)."""
+                 coarse_n2: int = 0, coarse_scheme: int = 0, **opts) -> hj_request:
+    """An hj_request for a workloads.ProblemSpec (coarse_n > 0: coarse
+    initialisation; coarse_n2: an intermediate level; coarse_scheme: the
+    scheme of the coarse levels)."""
     r = hj_request()
     r.coarse_n = int(coarse_n)
+    r.coarse_n2 = int(coarse_n2)
+    r.coarse_scheme = int(coarse_scheme)
     r.ndim = spec.ndim
     for i in range(spec.ndim):
         r.n[i] = int(spec.n[i])

@@ -135,7 +135,9 @@ def decomposed_update(n4: int = 61, n2: int = 201, nc4: int = 31, nc2: int = 101
 
 
 def adaptive_grid(nc: int = 31, nf: int = 81, b: float = 1.0,
-                  reference: Optional[Dict] = None) -> Dict:
+                  reference: Optional[Dict] = None,
+                  variants: Sequence[tuple] = (((41,), 0), ((21, 41), 0), ((31,), 2),
+                                               ((21, 41), 2))) -> Dict:
     """Coarse solve -> multilinear migration -> warm fine solve (Sec. III-C),
     against a cold fine solve.  With `reference` (41^4 oracle samples:
     indices and values), the fine results restricted to every second node
@@ -159,6 +161,31 @@ def adaptive_grid(nc: int = 31, nf: int = 81, b: float = 1.0,
     Wc = gf.value()
     gc.close()
     gf.close()
+    # more levels, and cheap gradients (ENO2) on the coarse levels
+    levels_out = []
+    for levels, coarse_scheme in variants:
+        grids = [hj.Grid.from_spec(wl.quad_x4(n, b)) for n in tuple(levels) + (nf,)]
+        _sync()
+        t5 = time.perf_counter()
+        steps = []
+        for k, g in enumerate(grids):
+            opts = dict(X4_OPTS)
+            if k < len(levels) and coarse_scheme:
+                opts["scheme"] = coarse_scheme
+            if k:
+                hj.prolong(grids[k - 1], g)
+            steps.append(g.solve(hj.HJ_WARM if k else hj.HJ_COLD, **opts)["steps"])
+        _sync()
+        ms = 1e3 * (time.perf_counter() - t5)
+        Wv = grids[-1].value()
+        for g in grids:
+            g.close()
+        levels_out.append(dict(levels=list(levels) + [nf],
+                               coarse_scheme="ENO2" if coarse_scheme == 2 else "WENO5",
+                               ms=ms, steps=steps, speedup_vs_cold=1e3 * (t4 - t3) / ms,
+                               sign_agreement=float(np.mean((Wv >= 0) == (Wc >= 0))),
+                               max_abs_diff_in_band=float(
+                                   np.abs(Wv - Wc)[np.abs(Wc) <= 0.5].max())))
     out = dict(coarse=dict(n=nc, ms=1e3 * (t1 - t0), steps=stc["steps"]),
                prolong_ms=1e3 * (t2 - t1),
                fine_warm=dict(n=nf, ms=1e3 * (t3 - t2), steps=stw["steps"],
@@ -169,7 +196,8 @@ def adaptive_grid(nc: int = 31, nf: int = 81, b: float = 1.0,
                sign_agreement=float(np.mean((Ww >= 0) == (Wc >= 0))),
                safe_fraction_adaptive=float(np.mean(Ww >= 0)),
                safe_fraction_cold=float(np.mean(Wc >= 0)),
-               max_abs_diff_in_band=float(np.abs(Ww - Wc)[np.abs(Wc) <= 0.5].max()))
+               max_abs_diff_in_band=float(np.abs(Ww - Wc)[np.abs(Wc) <= 0.5].max()),
+               levels=levels_out)
     if reference is not None and (nf - 1) % 40 == 0:
         r = (nf - 1) // 40
         idx = reference["idx"] * r
@@ -337,14 +365,18 @@ def load_reference(path: str) -> Optional[Dict]:
 def serving(count: int = 16, coarse_4d: int = 13) -> Dict:
     """The first `count` requests of the seeded serving trace through the
     server (default policy), through the server with coarse initialisation of
-    the 4-D requests, and through one-at-a-time cold solves."""
+    the 4-D requests (WENO5 on the coarse grid, and cheap ENO2 gradients
+    there), and through one-at-a-time cold solves."""
     trace = wl.serving_trace()[:count]
     a = serve.replay_server(trace)
     c = serve.replay_server(trace, coarse_4d=coarse_4d)
+    e = serve.replay_server(trace, coarse_4d=coarse_4d, coarse_scheme=hj.HJ_ENO2)
     b = serve.replay_fifo_cold(trace)
     keep = ("p50_ms", "p99_ms", "mean_ms", "wall_s", "updates_per_s")
     return dict(requests=count,
                 served={k: a[k] for k in keep},
                 served_coarse_init={k: c[k] for k in keep},
+                served_coarse_init_eno2={k: e[k] for k in keep},
                 plain_cold={k: b[k] for k in keep},
-                all_converged=all(s == 0 for s in a["statuses"] + b["statuses"] + c["statuses"]))
+                all_converged=all(s == 0 for s in a["statuses"] + b["statuses"] + c["statuses"]
+                                  + e["statuses"]))

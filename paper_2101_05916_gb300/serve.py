@@ -44,14 +44,15 @@ def solve_opts_for(req) -> Dict:
 def replay_server(trace: Sequence, budget_bytes: int = 40 << 30, max_active: int = 64,
                   time_scale: float = 1.0, warm: bool = True, stream=None,
                   order: int = hj.HJ_ORDER_SHORTEST, max_active_nodes: int = 6_000_000,
-                  coarse_4d: int = 0) -> Dict:
+                  coarse_4d: int = 0, coarse_levels: int = 1, coarse_scheme: int = 0) -> Dict:
     """Replay `trace` (workloads.Request list); returns latency stats.
 
     Default policy: shortest estimated work first, at most 6M nodes of large
     grids stepping at once (small grids ride along).  coarse_4d > 0 runs every
     4-D request with coarse initialisation (Sec. III-C) on a grid of
     max(coarse_4d, n/2) nodes per axis: exact or conservative, far fewer fine
-    steps."""
+    steps.  coarse_levels = 2 adds a coarser level of max(9, n/4) nodes below
+    it; coarse_scheme sets the coarse levels' scheme (0: the request's)."""
     s = hj.hj_server_create(budget_bytes, max_active, stream)
     hj.hj_server_set_policy(s, order, max_active_nodes)
     tickets: List[int] = [0] * len(trace)
@@ -62,12 +63,15 @@ def replay_server(trace: Sequence, budget_bytes: int = 40 << 30, max_active: int
             delay = r.arrival_s * time_scale - (time.perf_counter() - t0)
             if delay > 0:
                 time.sleep(delay)
-            cn = 0
+            cn, cn2 = 0, 0
             if coarse_4d and r.spec.ndim == 4:
                 cn = max(coarse_4d, min(r.spec.n) // 2)
                 cn = cn if cn < min(r.spec.n) else 0
+                if cn and coarse_levels == 2 and max(9, min(r.spec.n) // 4) < cn:
+                    cn, cn2 = max(9, min(r.spec.n) // 4), cn
             req = hj.make_request(r.spec, hj.HJ_WARM if warm else hj.HJ_COLD,
-                                  request_key(r.spec), coarse_n=cn, **solve_opts_for(r))
+                                  request_key(r.spec), coarse_n=cn, coarse_n2=cn2,
+                                  coarse_scheme=coarse_scheme, **solve_opts_for(r))
             tickets[i] = hj.hj_server_submit(s, req)
 
     th = threading.Thread(target=submit)

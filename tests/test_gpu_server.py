@@ -268,3 +268,36 @@ def test_translated_prior_warm_start(hj):
     g.close()
     assert st1["steps"] < stc["steps"]
     assert np.abs(W - Wc).max() <= REL * np.abs(Wc).max()
+
+
+def test_two_coarse_levels_and_coarse_scheme(hj):
+    """coarse_n -> coarse_n2 -> n inside the server, with cheap gradients
+    (ENO2) on the coarse levels: bit-identical to the same chain of calls by
+    hand (Sec. III-C)."""
+    from paper_2101_05916_gb300 import scenarios
+    spec = wl.quad_x4(25, 0.7)
+    opts = dict(scenarios.X4_OPTS, max_wall_ms=0.0)
+    s = hj.hj_server_create(4 << 30, 8)
+    req = hj.make_request(spec, hj.HJ_COLD, 0, coarse_n=9, coarse_n2=13,
+                          coarse_scheme=hj.HJ_ENO2, **opts)
+    rc, st, W = fetch(hj, s, hj.hj_server_submit(s, req), spec)
+    stats = hj.hj_server_get_stats(s)
+    assert rc == hj.HJ_OK and stats["completed"] == 1
+    assert stats["bytes_in_use"] >= 0
+    for bad in (dict(coarse_n=0, coarse_n2=13), dict(coarse_n=13, coarse_n2=9),
+                dict(coarse_n=9, coarse_scheme=4)):
+        with pytest.raises(hj.HJError):
+            hj.hj_server_submit(s, hj.make_request(spec, hj.HJ_COLD, 0, **bad, **opts))
+    hj.hj_server_destroy(s)
+    coarse = dict(opts, scheme=hj.HJ_ENO2)
+    g9, g13, g25 = (hj.Grid.from_spec(wl.quad_x4(n, 0.7)) for n in (9, 13, 25))
+    g9.solve(hj.HJ_COLD, **coarse)
+    hj.prolong(g9, g13)
+    g13.solve(hj.HJ_WARM, **coarse)
+    hj.prolong(g13, g25)
+    stw = g25.solve(hj.HJ_WARM, **opts)
+    Wm = g25.value()
+    for g in (g9, g13, g25):
+        g.close()
+    assert st["steps"] == stw["steps"]
+    assert np.array_equal(W, Wm)
