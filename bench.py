@@ -192,6 +192,15 @@ class ClockSampler:
 
 # ------------------------------------------------------------- reference arm
 
+def arm_config():
+    """The workload both arms report: the 41^4 x subsystem, WENO5, TVD-RK3."""
+    return {"workload": "x4_41^4_weno5_cold+warm_update", "grid": [N_AXIS] * 4,
+            "scheme": "WENO5", "rk": "TVD-RK3", "cfl": 0.5, "tol": 1e-4,
+            "check_dt": 0.1, "stop_band": BAND, "clamp": "monotone", "wind_prior": BOUND_PRIOR,
+            "wind": BOUND, "l2": "flushed between timed steps",
+            "parallelism": "independent grids per rank"}
+
+
 def run_reference(args):
     """The FP64 oracle as the reference arm: each step advances a bounded
     sample (2 TVD-RK3 steps of the 41^4 WENO5 x-subsystem) on the host cores."""
@@ -218,8 +227,9 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "x4_41^4_weno5_b0.5", "grid": [N_AXIS] * 4, "scheme": "WENO5",
-                   "sample": "%d TVD-RK3 steps per bench step" % sample_steps},
+        "config": dict(arm_config(),
+                       sample="%d TVD-RK3 steps of the same grid and scheme per bench step"
+                              % sample_steps),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "%d RK3 steps of 41^4 WENO5 per step, %d steps"
                                    % (sample_steps, args.steps)},
@@ -421,10 +431,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "x4_41^4_weno5_cold+warm_update", "grid": [N_AXIS] * 4,
-                   "scheme": "WENO5", "rk": "TVD-RK3", "cfl": 0.5, "tol": 1e-4,
-                   "check_dt": 0.1, "stop_band": BAND, "clamp": "monotone", "wind_prior": BOUND_PRIOR, "wind": BOUND,
-                   "l2": "flushed between timed steps", "parallelism": "independent grids per rank"},
+        "config": arm_config(),
         "latency_ms": latency,
         "roofline": roofline,
         "e2e": e2e,
