@@ -178,6 +178,8 @@ static hj_status run_window(hj_grid g, const hjd::DevGrid& d, int scheme, int cl
           g->g_clamp == clamp && g->g_band == band && g->g_margin == margin &&
           g->g_threads == g->threads)) {
       drop_graph(g);
+      // the shape-specialised kernels load outside the capture
+      hjk::jit_prepare(d, scheme, g->threads);
       cudaGraph_t graph = nullptr;
       HJ_CU(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
       unsigned long long before = hjk::g_launches.load();
@@ -571,6 +573,10 @@ hj_status hj_set_disturbance_field(hj_grid g, const float* d_lo, const float* d_
   invalidate(g);
   return HJ_OK;
 }
+
+void hj_set_jit(int enable) { hjk::jit_enable(enable); }
+
+long long hj_jit_kernels(void) { return hjk::jit_compiled(); }
 
 hj_status hj_autotune(hj_grid g, int scheme, int* threads_out) {
   if (!g) return fail(HJ_ERR_ARG, "grid is NULL");

@@ -400,6 +400,12 @@ hj_status Runner::round(bool use_graph) {
   if (use_graph) {
     auto it = graphs_.find(key);
     if (it == graphs_.end()) {
+      // grids launched on their own may use shape-specialised kernels,
+      // which load outside the capture
+      for (const Group& gr : groups_)
+        if (gr.pack.count == 1)
+          hjk::jit_prepare(gr.pack.items[0].g, gr.pack.items[0].kind % 10,
+                           slots_[gr.pack.items[0].slot].g->threads);
       cudaGraph_t graph = nullptr;
       HJ_CU(cudaStreamBeginCapture(cap_stream_, cudaStreamCaptureModeThreadLocal));
       cudaError_t e = enqueue_round(R, cap_stream_);

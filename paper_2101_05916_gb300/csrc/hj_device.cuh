@@ -13,9 +13,13 @@
 // worst-case disturbance sit at the ends of their intervals (bang-bang).
 #pragma once
 
+#ifdef __CUDACC_RTC__
+// compiled at run time (shape-specialised stage kernels): no host headers
+#define CUDART_INF_F __int_as_float(0x7f800000)
+#else
 #include <cuda_runtime.h>
 #include <math_constants.h>
-#include <stdint.h>
+#endif
 
 namespace hjd {
 
@@ -122,8 +126,8 @@ __device__ __forceinline__ float margin(const DevGrid& g, const float (&x)[D], i
 // when one is set (a GP confidence band, Sec. II-C), else the uniform box.
 __device__ __forceinline__ void dist_box(const DevGrid& g, int j, int node, float& lo, float& hi) {
   if (g.dflo) {
-    lo = __ldg(g.dflo + (size_t)j * g.npts + node);
-    hi = __ldg(g.dfhi + (size_t)j * g.npts + node);
+    lo = __ldg(g.dflo + (long long)j * g.npts + node);
+    hi = __ldg(g.dfhi + (long long)j * g.npts + node);
   } else {
     lo = g.dlo[j];
     hi = g.dhi[j];

@@ -16,9 +16,23 @@ extern std::atomic<unsigned long long> g_launches;
 constexpr int kStageThreads = 256;
 
 // One TVD-RK3 stage on one grid.  stage is 1, 2 or 3; scheme 1, 2 or 5;
-// threads per block 128, 256 or 512 (other values use 256).
+// threads per block 128, 256 or 512 (other values use 256).  allow_jit:
+// grids of at least kJitNodes nodes may run the shape-specialised kernel.
 cudaError_t launch_stage(const hjd::DevGrid& g, int scheme, int stage, const hjd::StageArgs& a,
-                         cudaStream_t s, int threads = kStageThreads);
+                         cudaStream_t s, int threads = kStageThreads, bool allow_jit = true);
+
+// Shape-specialised stage kernels (hj_jit.cu), compiled at run time for
+// grids of at least kJitNodes nodes.  jit_prepare compiles them for (grid
+// shape, scheme, threads) and must run outside any stream capture; inside a
+// capture jit_launch only uses kernels prepared before.  jit_launch sets
+// *used when it launched; otherwise the caller launches the precompiled one.
+constexpr long long kJitNodes = 1ll << 20;
+bool jit_wanted(const hjd::DevGrid& g);
+bool jit_prepare(const hjd::DevGrid& g, int scheme, int threads);
+cudaError_t jit_launch(const hjd::DevGrid& g, int scheme, int stage, const hjd::StageArgs& a,
+                       cudaStream_t s, int threads, bool* used);
+long long jit_compiled();
+void jit_enable(int on);
 // Per-axis max |f_i| over grid nodes and input vertices, as float bits into out[0..ndim).
 // out must be zeroed first.
 cudaError_t launch_alpha(const hjd::DevGrid& g, unsigned* out, cudaStream_t s);

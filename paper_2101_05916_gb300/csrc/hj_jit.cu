@@ -1,0 +1,236 @@
+// hj_jit.cu -- stage kernels specialised to one grid shape at run time.
+//
+// About a third of the stage kernel's instructions are index, address and
+// bounds arithmetic on the grid's axis lengths and strides.  For grids of at
+// least kJitNodes nodes the library compiles (NVRTC), on first use, the same
+// stage code with those integers folded in as constants, and keeps it for the
+// process.  Every node's floating-point arithmetic is the one of the
+// precompiled kernel; only integer index operations fold.  When NVRTC cannot
+// be loaded or a compilation fails, the precompiled kernel runs.
+#include <cuda_runtime.h>
+#include <dlfcn.h>
+#include <nvrtc.h>
+
+#include <atomic>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "hj_internal.h"
+
+// kJitHeaderNames / kJitHeaders: the device headers as text (build.py)
+#include "hj_jit_sources.inc"
+
+#ifndef HJ_CUDA_LIB64
+#define HJ_CUDA_LIB64 "/usr/local/cuda/lib64"
+#endif
+
+namespace hjk {
+namespace {
+
+// NVRTC entry points, loaded with dlopen so that the library does not need
+// NVRTC to load.
+struct Nvrtc {
+  decltype(&nvrtcCreateProgram) create = nullptr;
+  decltype(&nvrtcCompileProgram) compile = nullptr;
+  decltype(&nvrtcGetProgramLogSize) log_size = nullptr;
+  decltype(&nvrtcGetProgramLog) log = nullptr;
+  decltype(&nvrtcGetCUBINSize) cubin_size = nullptr;
+  decltype(&nvrtcGetCUBIN) cubin = nullptr;
+  decltype(&nvrtcDestroyProgram) destroy = nullptr;
+  bool ok = false;
+};
+
+const Nvrtc& nvrtc() {
+  static Nvrtc n = [] {
+    Nvrtc r;
+    const char* names[] = {"libnvrtc.so.13", HJ_CUDA_LIB64 "/libnvrtc.so.13", "libnvrtc.so"};
+    void* h = nullptr;
+    for (const char* nm : names)
+      if ((h = dlopen(nm, RTLD_NOW | RTLD_LOCAL))) break;
+    if (!h) return r;
+    r.create = (decltype(r.create))dlsym(h, "nvrtcCreateProgram");
+    r.compile = (decltype(r.compile))dlsym(h, "nvrtcCompileProgram");
+    r.log_size = (decltype(r.log_size))dlsym(h, "nvrtcGetProgramLogSize");
+    r.log = (decltype(r.log))dlsym(h, "nvrtcGetProgramLog");
+    r.cubin_size = (decltype(r.cubin_size))dlsym(h, "nvrtcGetCUBINSize");
+    r.cubin = (decltype(r.cubin))dlsym(h, "nvrtcGetCUBIN");
+    r.destroy = (decltype(r.destroy))dlsym(h, "nvrtcDestroyProgram");
+    r.ok = r.create && r.compile && r.log_size && r.log && r.cubin_size && r.cubin && r.destroy;
+    return r;
+  }();
+  return n;
+}
+
+struct Key {
+  int device, ndim, model, scheme, threads;
+  int n[hjd::MAXD];
+  bool operator<(const Key& o) const {
+    return std::memcmp(this, &o, sizeof(Key)) < 0;
+  }
+};
+
+struct Entry {
+  bool ok = false;
+  cudaLibrary_t lib = nullptr;
+  cudaKernel_t stage[3] = {nullptr, nullptr, nullptr};
+};
+
+std::mutex g_mu;
+std::map<Key, Entry> g_cache;
+std::atomic<long long> g_compiled{0};
+std::atomic<int> g_enabled{-1};  // -1: read HJ_JIT from the environment on first use
+
+bool enabled() {
+  int e = g_enabled.load();
+  if (e < 0) {
+    const char* v = std::getenv("HJ_JIT");
+    e = (v && v[0] == '0') ? 0 : 1;
+    g_enabled.store(e);
+  }
+  return e == 1;
+}
+
+Key key_of(const hjd::DevGrid& g, int scheme, int threads) {
+  Key k;
+  std::memset(&k, 0, sizeof(k));
+  cudaGetDevice(&k.device);
+  k.ndim = g.ndim;
+  k.model = g.model;
+  k.scheme = scheme;
+  k.threads = threads;
+  for (int d = 0; d < g.ndim; ++d) k.n[d] = g.n[d];
+  return k;
+}
+
+// The stage kernels of stage_kernel (hj_kernels.cu) with the shape fields
+// of the grid descriptor replaced by literals.
+std::string source(const hjd::DevGrid& g, int scheme, int threads) {
+  std::string s = "#include \"hj_stage.cuh\"\n";
+  s += "__device__ __forceinline__ hjd::DevGrid hj_fixed(const hjd::DevGrid& g) {\n";
+  s += "  hjd::DevGrid c = g;\n";
+  char buf[256];
+  for (int d = 0; d < g.ndim; ++d) {
+    std::snprintf(buf, sizeof(buf), "  c.n[%d] = %d; c.stride[%d] = %d;\n", d, g.n[d], d,
+                  g.stride[d]);
+    s += buf;
+  }
+  std::snprintf(buf, sizeof(buf),
+                "  c.npts = %d; c.plane = %d;\n  c.div_m[0] = %uu; c.div_s[0] = %d;\n"
+                "  c.div_m[1] = %uu; c.div_s[1] = %d;\n  return c;\n}\n",
+                g.npts, g.plane, g.div_m[0], g.div_s[0], g.div_m[1], g.div_s[1]);
+  s += buf;
+  for (int st = 1; st <= 3; ++st) {
+    std::snprintf(buf, sizeof(buf),
+                  "extern \"C\" __global__ void __launch_bounds__(%d)\n"
+                  "hj_stage_%d(const hjd::DevGrid g, const hjd::StageArgs a) {\n",
+                  threads, st);
+    s += buf;
+    std::snprintf(buf, sizeof(buf),
+                  "  unsigned r = hjd::stage_point<%d, %d, %d, %d>(hj_fixed(g), a,\n"
+                  "      blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y, a.check != 0);\n",
+                  g.ndim, scheme, g.model, st);
+    s += buf;
+    if (st == 3) s += "  if (a.check) hjd::block_max_bits(r, a.resid);\n";
+    else s += "  (void)r;\n";
+    s += "}\n";
+  }
+  return s;
+}
+
+Entry build(const hjd::DevGrid& g, int scheme, int threads) {
+  Entry e;
+  const Nvrtc& n = nvrtc();
+  if (!n.ok) return e;
+  std::string src = source(g, scheme, threads);
+  nvrtcProgram prog = nullptr;
+  int nh = (int)(sizeof(kJitHeaders) / sizeof(kJitHeaders[0]));
+  if (n.create(&prog, src.c_str(), "hj_stage_jit.cu", nh, kJitHeaders, kJitHeaderNames) !=
+      NVRTC_SUCCESS)
+    return e;
+  const char* opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-ftz=true", "-lineinfo"};
+  nvrtcResult rc = n.compile(prog, 4, opts);
+  size_t sz = 0;
+  std::vector<char> cubin;
+  if (rc == NVRTC_SUCCESS && n.cubin_size(prog, &sz) == NVRTC_SUCCESS && sz > 0) {
+    cubin.resize(sz);
+    if (n.cubin(prog, cubin.data()) != NVRTC_SUCCESS) cubin.clear();
+  }
+  n.destroy(&prog);
+  if (cubin.empty()) return e;
+  if (cudaLibraryLoadData(&e.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    e.lib = nullptr;
+    return e;
+  }
+  for (int st = 0; st < 3; ++st) {
+    char name[32];
+    std::snprintf(name, sizeof(name), "hj_stage_%d", st + 1);
+    if (cudaLibraryGetKernel(&e.stage[st], e.lib, name) != cudaSuccess) {
+      cudaGetLastError();
+      cudaLibraryUnload(e.lib);
+      return Entry();
+    }
+  }
+  e.ok = true;
+  g_compiled.fetch_add(1);
+  return e;
+}
+
+}  // namespace
+
+bool jit_wanted(const hjd::DevGrid& g) {
+  return (long long)g.npts >= kJitNodes && enabled();
+}
+
+bool jit_prepare(const hjd::DevGrid& g, int scheme, int threads) {
+  if (!jit_wanted(g)) return false;
+  Key k = key_of(g, scheme, threads);
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_cache.find(k);
+  if (it == g_cache.end()) it = g_cache.emplace(k, build(g, scheme, threads)).first;
+  return it->second.ok;
+}
+
+cudaError_t jit_launch(const hjd::DevGrid& g, int scheme, int stage, const hjd::StageArgs& a,
+                       cudaStream_t s, int threads, bool* used) {
+  *used = false;
+  if (!jit_wanted(g)) return cudaSuccess;
+  Key k = key_of(g, scheme, threads);
+  cudaKernel_t kern = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_cache.find(k);
+    if (it == g_cache.end()) {
+      // compile only outside a stream capture; a capture falls back to the
+      // precompiled kernel unless jit_prepare ran before it
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return cudaSuccess;
+      it = g_cache.emplace(k, build(g, scheme, threads)).first;
+    }
+    if (!it->second.ok) return cudaSuccess;
+    kern = it->second.stage[stage - 1];
+  }
+  unsigned bx = (unsigned)((g.plane + threads - 1) / threads);
+  unsigned by = g.ndim == 4 ? (unsigned)g.n[0] : 1u;
+  void* args[] = {(void*)&g, (void*)&a};
+  cudaError_t e = cudaLaunchKernel((const void*)kern, dim3(bx, by, 1), dim3(threads, 1, 1), args,
+                                   0, s);
+  if (e == cudaSuccess) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    *used = true;
+  }
+  return e;
+}
+
+long long jit_compiled() { return g_compiled.load(); }
+
+void jit_enable(int on) { g_enabled.store(on ? 1 : 0); }
+
+}  // namespace hjk

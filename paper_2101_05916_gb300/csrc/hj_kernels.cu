@@ -223,7 +223,13 @@ bool stage_supported(int model, int ndim, int scheme) {
 }
 
 cudaError_t launch_stage(const DevGrid& g, int scheme, int stage, const StageArgs& a, cudaStream_t s,
-                         int threads) {
+                         int threads, bool allow_jit) {
+  if (threads != 128 && threads != 512) threads = 256;
+  if (allow_jit) {
+    bool used = false;
+    cudaError_t e = jit_launch(g, scheme, stage, a, s, threads, &used);
+    if (used || e != cudaSuccess) return e;
+  }
   switch (g.model) {
     case hjd::M_QUAD_Z: return stage_by_scheme<2, hjd::M_QUAD_Z>(g, scheme, stage, a, threads, s);
     case hjd::M_QUAD_X4: return stage_by_scheme<4, hjd::M_QUAD_X4>(g, scheme, stage, a, threads, s);

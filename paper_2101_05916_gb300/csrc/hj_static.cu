@@ -198,9 +198,9 @@ extern "C" hj_status hj_solve_fixed_static(int ndim, const int* n, const double*
     hjd::StageArgs a2{A, Wk, B, nullptr, nullptr, fdt, 0, clamp, 0.f};
     hjd::StageArgs a3{B, Wk, Wk, nullptr, nullptr, fdt, 0, clamp, 0.f};
     for (long long k = 0; k < steps; ++k) {
-      HJ_CU(hjk::launch_stage(d, scheme, 1, a1, s));
-      HJ_CU(hjk::launch_stage(d, scheme, 2, a2, s));
-      HJ_CU(hjk::launch_stage(d, scheme, 3, a3, s));
+      HJ_CU(hjk::launch_stage(d, scheme, 1, a1, s, hjk::kStageThreads, false));
+      HJ_CU(hjk::launch_stage(d, scheme, 2, a2, s, hjk::kStageThreads, false));
+      HJ_CU(hjk::launch_stage(d, scheme, 3, a3, s, hjk::kStageThreads, false));
     }
   }
   HJ_CU(cudaMemcpyAsync(W, Wk, wbytes, cudaMemcpyDeviceToDevice, s));

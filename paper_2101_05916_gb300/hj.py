@@ -100,6 +100,8 @@ SIGNATURES = {
                             _P(_i)]),
     "hj_prolong": (_i, [_vp, _vp]),
     "hj_translate": (_i, [_vp, _vp, _P(_d)]),
+    "hj_set_jit": (None, [_i]),
+    "hj_jit_kernels": (_ll, []),
     "hj_set_value": (_i, [_vp, _vp, _i]),
     "hj_get_value": (_i, [_vp, _vp, _i]),
     "hj_query_value": (_i, [_vp, _i, _P(_d), _P(_d)]),
@@ -388,6 +390,14 @@ def hj_safety_filter(grids, axes, ctrl_index, states, u_perf, level: float = 0.0
                                   sd, cd, nq, x.ctypes.data, up.ctypes.data, float(level),
                                   u.ctypes.data, w.ctypes.data, act.ctypes.data, 0))
     return u, w, act
+
+
+def hj_set_jit(enable: bool) -> None:
+    lib().hj_set_jit(1 if enable else 0)
+
+
+def hj_jit_kernels() -> int:
+    return int(lib().hj_jit_kernels())
 
 
 def hj_autotune(g: int, scheme: int = HJ_WENO5) -> int:

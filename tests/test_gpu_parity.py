@@ -706,3 +706,30 @@ def test_autotune_keeps_value_and_results(hj):
     dt = oracle.cfl_dt(spec)
     Wo, _ = oracle.solve(spec, scheme=5, dt=st1["dt"], fixed_steps=7)
     assert_parity(W1, Wo, spec)
+
+
+def test_shape_specialised_kernels_match_precompiled_bitwise(hj):
+    """Grids of >= 2^20 nodes run stage kernels compiled at run time with the
+    grid shape as constants: the same values as the precompiled kernels,
+    bit for bit, on direct launches and inside captured graphs."""
+    cases = [(wl.quad_x4(33, 0.5), 5), (wl.quad_z(1025, 0.5), 2)]
+    before = hj.hj_jit_kernels()
+    out = {}
+    try:
+        for jit in (True, False):
+            hj.hj_set_jit(jit)
+            for spec, scheme in cases:
+                g = hj.Grid.from_spec(spec)
+                g.solve(hj.HJ_COLD, scheme=scheme, fixed_steps=6, use_graph=False)
+                Wd = g.value()
+                st = g.solve(hj.HJ_COLD, scheme=scheme, tol=1e-2, max_steps=400)
+                Wg = g.value()
+                g.close()
+                out[(jit, spec.name)] = (Wd, Wg, st["steps"])
+    finally:
+        hj.hj_set_jit(True)
+    assert hj.hj_jit_kernels() > before
+    for spec, _ in cases:
+        a, b = out[(True, spec.name)], out[(False, spec.name)]
+        assert a[2] == b[2]
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
