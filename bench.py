@@ -62,7 +62,7 @@ BYTES_PER_UPDATE = 32.0
 # DRAM bytes per stage launch (read + write, average of stages 1-3) from the
 # ncu capture summarised in profiles/stage_kernel_x41_weno5.md; set to None
 # whenever the stage kernel changes until it is captured again.
-STAGE_TRAFFIC_BYTES = (11.319040e6 + 22.621696e6 + 22.627072e6) / 3.0
+STAGE_TRAFFIC_BYTES = (11.317248e6 + 22.620160e6 + 22.624512e6) / 3.0
 # FP32 non-tensor peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
@@ -354,7 +354,9 @@ def main():
     hbm_gbs = BYTES_PER_UPDATE / 3.0 * npts / per_launch_s / 1e9
     peaks = measured_peaks()
     roofline = {
-        "bound": "alu", "kernel": "stage_kernel<4,WENO5,quad_x4>",
+        "bound": "alu",
+        "kernel": ("hj_stage_1..3 (stage kernel, WENO5, quad_x4, specialised to the 41^4 shape)"
+                   if hj.hj_jit_kernels() > 0 else "stage_kernel<4,WENO5,quad_x4>"),
         "achieved": achieved_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
         "frac": achieved_tflops / FP32_PEAK_TFLOPS,
         "peak_source": "FP32 lanes x max SM clock (152 x 128 x 2 x 2.07 GHz)",
