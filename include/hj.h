@@ -456,15 +456,19 @@ hj_status hj_solve_fixed_static(int ndim, const int* n, const double* lo, const 
 hj_status hj_autotune(hj_grid g, int scheme, int* threads_out);
 
 /* Shape-specialised stage kernels.  For grids of at least 2^20 nodes the
- * library compiles at run time (NVRTC, on first use per grid shape, scheme
- * and block size) the stage kernels with the grid's axis lengths and
+ * library compiles at run time (NVRTC, from the first use per grid shape,
+ * scheme and block size) the stage kernels with the grid's axis lengths and
  * strides as constants, and keeps them for the process: the same arithmetic
  * per node with fewer index instructions.  Where NVRTC is not available or
  * a compilation fails, the precompiled kernels run.
+ * The compile runs on a background thread: solves never wait for it, and
+ * use the specialised kernels from the first launch after it finished.
  * hj_set_jit(0) turns this off (also HJ_JIT=0 in the environment), 1 on.
- * hj_jit_kernels() counts the kernel sets compiled so far. */
+ * hj_jit_kernels() counts the kernel sets loaded so far; hj_jit_pending()
+ * the compiles still running. */
 void hj_set_jit(int enable);
 long long hj_jit_kernels(void);
+long long hj_jit_pending(void);
 
 /* Number of nodes of the grid. */
 long long hj_grid_points(hj_grid g);

@@ -174,12 +174,14 @@ static cudaError_t enqueue_window(hj_grid g, const hjd::DevGrid& d, int scheme, 
 static hj_status run_window(hj_grid g, const hjd::DevGrid& d, int scheme, int clamp, float band,
                             int margin, float dt, long long k, bool use_graph) {
   if (use_graph && k <= 4096) {
+    // shape-specialised kernels load outside the capture; a graph captured
+    // before they were ready is rebuilt once they are
+    bool jit = hjk::jit_prepare(d, scheme, g->threads);
     if (!(g->gexec && g->g_per == k && g->g_dt == dt && g->g_scheme == scheme &&
           g->g_clamp == clamp && g->g_band == band && g->g_margin == margin &&
-          g->g_threads == g->threads)) {
+          g->g_threads == g->threads && g->g_jit == jit)) {
       drop_graph(g);
-      // the shape-specialised kernels load outside the capture
-      hjk::jit_prepare(d, scheme, g->threads);
+      g->g_jit = jit;
       cudaGraph_t graph = nullptr;
       HJ_CU(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
       unsigned long long before = hjk::g_launches.load();
@@ -577,6 +579,8 @@ hj_status hj_set_disturbance_field(hj_grid g, const float* d_lo, const float* d_
 void hj_set_jit(int enable) { hjk::jit_enable(enable); }
 
 long long hj_jit_kernels(void) { return hjk::jit_compiled(); }
+
+long long hj_jit_pending(void) { return hjk::jit_pending(); }
 
 hj_status hj_autotune(hj_grid g, int scheme, int* threads_out) {
   if (!g) return fail(HJ_ERR_ARG, "grid is NULL");

@@ -396,16 +396,18 @@ hj_status Runner::round(bool use_graph) {
       long long to_cap = c.max_steps - c.steps;
       key += "," + std::to_string(c.steps % c.per) + ":" + std::to_string(to_cap <= R ? to_cap : -1);
     }
+  // grids launched on their own may use shape-specialised kernels: they
+  // load outside the capture, and a round graph records whether it has them
+  for (const Group& gr : groups_)
+    if (gr.pack.count == 1)
+      key += hjk::jit_prepare(gr.pack.items[0].g, gr.pack.items[0].kind % 10,
+                              slots_[gr.pack.items[0].slot].g->threads)
+                 ? "j"
+                 : "p";
   unsigned long long before = hjk::g_launches.load();
   if (use_graph) {
     auto it = graphs_.find(key);
     if (it == graphs_.end()) {
-      // grids launched on their own may use shape-specialised kernels,
-      // which load outside the capture
-      for (const Group& gr : groups_)
-        if (gr.pack.count == 1)
-          hjk::jit_prepare(gr.pack.items[0].g, gr.pack.items[0].kind % 10,
-                           slots_[gr.pack.items[0].slot].g->threads);
       cudaGraph_t graph = nullptr;
       HJ_CU(cudaStreamBeginCapture(cap_stream_, cudaStreamCaptureModeThreadLocal));
       cudaError_t e = enqueue_round(R, cap_stream_);

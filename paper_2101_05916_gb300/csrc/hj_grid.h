@@ -55,6 +55,7 @@ struct hj_grid_s {
   float g_band = 0.f;
   int g_margin = 0;
   int g_threads = 0;
+  bool g_jit = false;  // the cached graph holds shape-specialised kernels
 };
 
 namespace hja {

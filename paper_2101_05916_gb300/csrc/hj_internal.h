@@ -22,16 +22,18 @@ cudaError_t launch_stage(const hjd::DevGrid& g, int scheme, int stage, const hjd
                          cudaStream_t s, int threads = kStageThreads, bool allow_jit = true);
 
 // Shape-specialised stage kernels (hj_jit.cu), compiled at run time for
-// grids of at least kJitNodes nodes.  jit_prepare compiles them for (grid
-// shape, scheme, threads) and must run outside any stream capture; inside a
-// capture jit_launch only uses kernels prepared before.  jit_launch sets
-// *used when it launched; otherwise the caller launches the precompiled one.
+// grids of at least kJitNodes nodes.  The first sight of (grid shape,
+// scheme, threads) starts a background compile; jit_prepare loads a
+// finished one (outside any stream capture) and says whether the kernels
+// are ready.  jit_launch sets *used when it launched; otherwise the caller
+// launches the precompiled one.
 constexpr long long kJitNodes = 1ll << 20;
 bool jit_wanted(const hjd::DevGrid& g);
 bool jit_prepare(const hjd::DevGrid& g, int scheme, int threads);
 cudaError_t jit_launch(const hjd::DevGrid& g, int scheme, int stage, const hjd::StageArgs& a,
                        cudaStream_t s, int threads, bool* used);
 long long jit_compiled();
+long long jit_pending();
 void jit_enable(int on);
 // Per-axis max |f_i| over grid nodes and input vertices, as float bits into out[0..ndim).
 // out must be zeroed first.

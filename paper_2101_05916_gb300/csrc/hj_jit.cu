@@ -2,11 +2,13 @@
 //
 // About a third of the stage kernel's instructions are index, address and
 // bounds arithmetic on the grid's axis lengths and strides.  For grids of at
-// least kJitNodes nodes the library compiles (NVRTC), on first use, the same
-// stage code with those integers folded in as constants, and keeps it for the
-// process.  Every node's floating-point arithmetic is the one of the
-// precompiled kernel; only integer index operations fold.  When NVRTC cannot
-// be loaded or a compilation fails, the precompiled kernel runs.
+// least kJitNodes nodes the library compiles (NVRTC), from the first use on,
+// the same stage code with those integers folded in as constants, and keeps
+// it for the process.  The compile runs on a background thread; until it is
+// loaded the precompiled kernel runs, so no solve waits for it.  Every
+// node's floating-point arithmetic is the one of the precompiled kernel;
+// only integer index operations fold.  When NVRTC cannot be loaded or a
+// compilation fails, the precompiled kernel runs.
 #include <cuda_runtime.h>
 #include <dlfcn.h>
 #include <nvrtc.h>
@@ -16,8 +18,10 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "hj_internal.h"
@@ -74,15 +78,19 @@ struct Key {
   }
 };
 
+// One kernel set: compiled on a background thread (NVRTC only, no CUDA
+// calls there), then loaded on a caller's thread outside any capture.
 struct Entry {
-  bool ok = false;
+  std::atomic<int> state{0};  // 0 compiling, 1 cubin ready, 2 loaded, 3 failed
+  std::vector<char> cubin;
   cudaLibrary_t lib = nullptr;
   cudaKernel_t stage[3] = {nullptr, nullptr, nullptr};
 };
 
 std::mutex g_mu;
-std::map<Key, Entry> g_cache;
+std::map<Key, std::shared_ptr<Entry>> g_cache;
 std::atomic<long long> g_compiled{0};
+std::atomic<long long> g_pending{0};
 std::atomic<int> g_enabled{-1};  // -1: read HJ_JIT from the environment on first use
 
 bool enabled() {
@@ -142,31 +150,35 @@ std::string source(const hjd::DevGrid& g, int scheme, int threads) {
   return s;
 }
 
-Entry build(const hjd::DevGrid& g, int scheme, int threads) {
-  Entry e;
+// NVRTC compile of one kernel set (no CUDA calls).
+std::vector<char> compile(const std::string& src) {
+  std::vector<char> cubin;
   const Nvrtc& n = nvrtc();
-  if (!n.ok) return e;
-  std::string src = source(g, scheme, threads);
+  if (!n.ok) return cubin;
   nvrtcProgram prog = nullptr;
   int nh = (int)(sizeof(kJitHeaders) / sizeof(kJitHeaders[0]));
   if (n.create(&prog, src.c_str(), "hj_stage_jit.cu", nh, kJitHeaders, kJitHeaderNames) !=
       NVRTC_SUCCESS)
-    return e;
+    return cubin;
   const char* opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-ftz=true", "-lineinfo"};
-  nvrtcResult rc = n.compile(prog, 4, opts);
   size_t sz = 0;
-  std::vector<char> cubin;
-  if (rc == NVRTC_SUCCESS && n.cubin_size(prog, &sz) == NVRTC_SUCCESS && sz > 0) {
+  if (n.compile(prog, 4, opts) == NVRTC_SUCCESS && n.cubin_size(prog, &sz) == NVRTC_SUCCESS &&
+      sz > 0) {
     cubin.resize(sz);
     if (n.cubin(prog, cubin.data()) != NVRTC_SUCCESS) cubin.clear();
   }
   n.destroy(&prog);
-  if (cubin.empty()) return e;
-  if (cudaLibraryLoadData(&e.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) !=
+  return cubin;
+}
+
+// Load a compiled set on this thread (never inside a capture).
+void load(Entry& e) {
+  if (cudaLibraryLoadData(&e.lib, e.cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) !=
       cudaSuccess) {
     cudaGetLastError();
     e.lib = nullptr;
-    return e;
+    e.state.store(3);
+    return;
   }
   for (int st = 0; st < 3; ++st) {
     char name[32];
@@ -174,12 +186,58 @@ Entry build(const hjd::DevGrid& g, int scheme, int threads) {
     if (cudaLibraryGetKernel(&e.stage[st], e.lib, name) != cudaSuccess) {
       cudaGetLastError();
       cudaLibraryUnload(e.lib);
-      return Entry();
+      e.lib = nullptr;
+      e.state.store(3);
+      return;
     }
   }
-  e.ok = true;
+  e.cubin.clear();
+  e.state.store(2);
   g_compiled.fetch_add(1);
-  return e;
+}
+
+bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+// The entry of (grid shape, scheme, threads): started on first sight,
+// loaded once compiled when `may_load`.  Returns it when loaded.
+Entry* lookup(const hjd::DevGrid& g, int scheme, int threads, bool may_load) {
+  Key k = key_of(g, scheme, threads);
+  std::shared_ptr<Entry> e;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_cache.find(k);
+    if (it == g_cache.end()) {
+      e = std::make_shared<Entry>();
+      g_cache.emplace(k, e);
+      if (!nvrtc().ok) {
+        e->state.store(3);
+        return nullptr;
+      }
+      g_pending.fetch_add(1);
+      std::string src = source(g, scheme, threads);
+      std::thread([e, src] {
+        e->cubin = compile(src);
+        e->state.store(e->cubin.empty() ? 3 : 1);
+        g_pending.fetch_sub(1);
+      }).detach();
+      return nullptr;
+    }
+    e = it->second;
+  }
+  int st = e->state.load();
+  if (st == 1 && may_load) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (e->state.load() == 1) load(*e);
+    st = e->state.load();
+  }
+  return st == 2 ? e.get() : nullptr;
 }
 
 }  // namespace
@@ -190,46 +248,30 @@ bool jit_wanted(const hjd::DevGrid& g) {
 
 bool jit_prepare(const hjd::DevGrid& g, int scheme, int threads) {
   if (!jit_wanted(g)) return false;
-  Key k = key_of(g, scheme, threads);
-  std::lock_guard<std::mutex> lk(g_mu);
-  auto it = g_cache.find(k);
-  if (it == g_cache.end()) it = g_cache.emplace(k, build(g, scheme, threads)).first;
-  return it->second.ok;
+  return lookup(g, scheme, threads, true) != nullptr;
 }
 
 cudaError_t jit_launch(const hjd::DevGrid& g, int scheme, int stage, const hjd::StageArgs& a,
                        cudaStream_t s, int threads, bool* used) {
   *used = false;
   if (!jit_wanted(g)) return cudaSuccess;
-  Key k = key_of(g, scheme, threads);
-  cudaKernel_t kern = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(g_mu);
-    auto it = g_cache.find(k);
-    if (it == g_cache.end()) {
-      // compile only outside a stream capture; a capture falls back to the
-      // precompiled kernel unless jit_prepare ran before it
-      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-      if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
-        return cudaSuccess;
-      it = g_cache.emplace(k, build(g, scheme, threads)).first;
-    }
-    if (!it->second.ok) return cudaSuccess;
-    kern = it->second.stage[stage - 1];
-  }
+  Entry* e = lookup(g, scheme, threads, !capturing(s));
+  if (!e) return cudaSuccess;
   unsigned bx = (unsigned)((g.plane + threads - 1) / threads);
   unsigned by = g.ndim == 4 ? (unsigned)g.n[0] : 1u;
   void* args[] = {(void*)&g, (void*)&a};
-  cudaError_t e = cudaLaunchKernel((const void*)kern, dim3(bx, by, 1), dim3(threads, 1, 1), args,
-                                   0, s);
-  if (e == cudaSuccess) {
+  cudaError_t err = cudaLaunchKernel((const void*)e->stage[stage - 1], dim3(bx, by, 1),
+                                     dim3(threads, 1, 1), args, 0, s);
+  if (err == cudaSuccess) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
     *used = true;
   }
-  return e;
+  return err;
 }
 
 long long jit_compiled() { return g_compiled.load(); }
+
+long long jit_pending() { return g_pending.load(); }
 
 void jit_enable(int on) { g_enabled.store(on ? 1 : 0); }
 

@@ -102,6 +102,7 @@ SIGNATURES = {
     "hj_translate": (_i, [_vp, _vp, _P(_d)]),
     "hj_set_jit": (None, [_i]),
     "hj_jit_kernels": (_ll, []),
+    "hj_jit_pending": (_ll, []),
     "hj_set_value": (_i, [_vp, _vp, _i]),
     "hj_get_value": (_i, [_vp, _vp, _i]),
     "hj_query_value": (_i, [_vp, _i, _P(_d), _P(_d)]),
@@ -398,6 +399,22 @@ def hj_set_jit(enable: bool) -> None:
 
 def hj_jit_kernels() -> int:
     return int(lib().hj_jit_kernels())
+
+
+def hj_jit_pending() -> int:
+    return int(lib().hj_jit_pending())
+
+
+def hj_jit_wait(timeout_s: float = 120.0) -> bool:
+    """Wait until no shape-specialised compile is running (True) or the
+    timeout passed (False)."""
+    import time
+    t0 = time.perf_counter()
+    while hj_jit_pending() > 0:
+        if time.perf_counter() - t0 > timeout_s:
+            return False
+        time.sleep(0.01)
+    return True
 
 
 def hj_autotune(g: int, scheme: int = HJ_WENO5) -> int:

@@ -720,6 +720,9 @@ def test_shape_specialised_kernels_match_precompiled_bitwise(hj):
             hj.hj_set_jit(jit)
             for spec, scheme in cases:
                 g = hj.Grid.from_spec(spec)
+                # the first launch starts the background compile; wait for it
+                g.solve(hj.HJ_COLD, scheme=scheme, fixed_steps=1, use_graph=False)
+                assert hj.hj_jit_wait(120.0)
                 g.solve(hj.HJ_COLD, scheme=scheme, fixed_steps=6, use_graph=False)
                 Wd = g.value()
                 st = g.solve(hj.HJ_COLD, scheme=scheme, tol=1e-2, max_steps=400)
