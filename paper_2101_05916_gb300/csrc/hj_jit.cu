@@ -70,13 +70,32 @@ const Nvrtc& nvrtc() {
   return n;
 }
 
+// Everything folded into a kernel set: the shape, and the geometry and
+// model constants that stay fixed while a grid is updated (the disturbance
+// bound, alpha and the constraint box stay run-time values).
 struct Key {
-  int device, ndim, model, scheme, threads;
+  int device, ndim, model, scheme, threads, con_kind;
+  unsigned con_mask;
   int n[hjd::MAXD];
+  unsigned geom[5 * hjd::MAXD];  // float bits of lo, h, ih, hih, wfloor
+  unsigned prm[8];               // float bits of the model parameters
   bool operator<(const Key& o) const {
     return std::memcmp(this, &o, sizeof(Key)) < 0;
   }
 };
+
+unsigned bits(float v) {
+  unsigned u;
+  std::memcpy(&u, &v, sizeof(u));
+  return u;
+}
+
+// An exact float literal (hexadecimal).
+std::string flit(float v) {
+  char buf[64];
+  std::snprintf(buf, sizeof(buf), "%af", (double)v);
+  return buf;
+}
 
 // One kernel set: compiled on a background thread (NVRTC only, no CUDA
 // calls there), then loaded on a caller's thread outside any capture.
@@ -111,7 +130,17 @@ Key key_of(const hjd::DevGrid& g, int scheme, int threads) {
   k.model = g.model;
   k.scheme = scheme;
   k.threads = threads;
-  for (int d = 0; d < g.ndim; ++d) k.n[d] = g.n[d];
+  k.con_kind = g.con_kind;
+  k.con_mask = g.con_mask;
+  for (int d = 0; d < g.ndim; ++d) {
+    k.n[d] = g.n[d];
+    k.geom[5 * d + 0] = bits(g.lo[d]);
+    k.geom[5 * d + 1] = bits(g.h[d]);
+    k.geom[5 * d + 2] = bits(g.ih[d]);
+    k.geom[5 * d + 3] = bits(g.hih[d]);
+    k.geom[5 * d + 4] = bits(g.wfloor[d]);
+  }
+  for (int i = 0; i < 8; ++i) k.prm[i] = bits(g.prm[i]);
   return k;
 }
 
@@ -126,7 +155,16 @@ std::string source(const hjd::DevGrid& g, int scheme, int threads) {
     std::snprintf(buf, sizeof(buf), "  c.n[%d] = %d; c.stride[%d] = %d;\n", d, g.n[d], d,
                   g.stride[d]);
     s += buf;
+    s += "  c.lo[" + std::to_string(d) + "] = " + flit(g.lo[d]) + "; c.h[" + std::to_string(d) +
+         "] = " + flit(g.h[d]) + "; c.ih[" + std::to_string(d) + "] = " + flit(g.ih[d]) + ";\n";
+    s += "  c.hih[" + std::to_string(d) + "] = " + flit(g.hih[d]) + "; c.wfloor[" +
+         std::to_string(d) + "] = " + flit(g.wfloor[d]) + ";\n";
   }
+  for (int i = 0; i < 8; ++i)
+    s += "  c.prm[" + std::to_string(i) + "] = " + flit(g.prm[i]) + ";\n";
+  std::snprintf(buf, sizeof(buf), "  c.con_kind = %d; c.con_mask = %uu;\n", g.con_kind,
+                g.con_mask);
+  s += buf;
   std::snprintf(buf, sizeof(buf),
                 "  c.npts = %d; c.plane = %d;\n  c.div_m[0] = %uu; c.div_s[0] = %d;\n"
                 "  c.div_m[1] = %uu; c.div_s[1] = %d;\n  return c;\n}\n",
