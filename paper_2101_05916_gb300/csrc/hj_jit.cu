@@ -14,6 +14,8 @@
 #include <nvrtc.h>
 
 #include <atomic>
+#include <chrono>
+#include <condition_variable>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -209,6 +211,42 @@ std::vector<char> compile(const std::string& src) {
   return cubin;
 }
 
+// At most kMaxCompiles compiles run at once: a server that meets many new
+// shapes must not take every host core from its own thread.
+constexpr int kMaxCompiles = 4;
+std::mutex g_slot_mu;
+std::condition_variable g_slot_cv;
+int g_slots_used = 0;
+
+// Exit waits (bounded) for compiles still running, so that none is inside
+// NVRTC while the process tears its libraries down.  Registered on the first
+// compile, i.e. after NVRTC was loaded, so it runs before NVRTC's teardown.
+void wait_pending_at_exit() {
+  for (int i = 0; i < 6000 && g_pending.load() > 0; ++i)
+    std::this_thread::sleep_for(std::chrono::milliseconds(10));
+}
+
+void compile_async(std::shared_ptr<Entry> e, std::string src) {
+  static const bool registered = (std::atexit(wait_pending_at_exit), true);
+  (void)registered;
+  g_pending.fetch_add(1);
+  std::thread([e, src] {
+    {
+      std::unique_lock<std::mutex> lk(g_slot_mu);
+      g_slot_cv.wait(lk, [] { return g_slots_used < kMaxCompiles; });
+      ++g_slots_used;
+    }
+    e->cubin = compile(src);
+    e->state.store(e->cubin.empty() ? 3 : 1);
+    {
+      std::lock_guard<std::mutex> lk(g_slot_mu);
+      --g_slots_used;
+    }
+    g_slot_cv.notify_one();
+    g_pending.fetch_sub(1);
+  }).detach();
+}
+
 // Load a compiled set on this thread (never inside a capture).
 void load(Entry& e) {
   if (cudaLibraryLoadData(&e.lib, e.cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) !=
@@ -258,13 +296,7 @@ Entry* lookup(const hjd::DevGrid& g, int scheme, int threads, bool may_load) {
         e->state.store(3);
         return nullptr;
       }
-      g_pending.fetch_add(1);
-      std::string src = source(g, scheme, threads);
-      std::thread([e, src] {
-        e->cubin = compile(src);
-        e->state.store(e->cubin.empty() ? 3 : 1);
-        g_pending.fetch_sub(1);
-      }).detach();
+      compile_async(e, source(g, scheme, threads));
       return nullptr;
     }
     e = it->second;

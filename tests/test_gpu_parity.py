@@ -736,3 +736,19 @@ def test_shape_specialised_kernels_match_precompiled_bitwise(hj):
         a, b = out[(True, spec.name)], out[(False, spec.name)]
         assert a[2] == b[2]
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_exit_with_a_compile_running_is_clean(hj):
+    """A process that exits while a shape-specialised compile still runs
+    (it waits for it at exit) ends with status 0."""
+    import subprocess
+    import sys
+    code = ("from paper_2101_05916_gb300 import hj, workloads as wl\n"
+            "g = hj.Grid.from_spec(wl.quad_x4(35, 0.5))\n"
+            "g.solve(hj.HJ_COLD, scheme=5, fixed_steps=1, use_graph=False)\n"
+            "print('pending', hj.hj_jit_pending())\n")
+    root = __file__.rsplit("/tests/", 1)[0]
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert "pending" in r.stdout
