@@ -62,7 +62,7 @@ BYTES_PER_UPDATE = 32.0
 # DRAM bytes per stage launch (read + write, average of stages 1-3) from the
 # ncu capture summarised in profiles/stage_kernel_x41_weno5.md; set to None
 # whenever the stage kernel changes until it is captured again.
-STAGE_TRAFFIC_BYTES = (11.317248e6 + 22.620160e6 + 22.624512e6) / 3.0
+STAGE_TRAFFIC_BYTES = (11.316736e6 + 22.620416e6 + 22.622720e6) / 3.0
 # FP32 non-tensor peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
