@@ -417,6 +417,44 @@ def hj_jit_wait(timeout_s: float = 120.0) -> bool:
     return True
 
 
+class SafetyFilter:
+    """hj_safety_filter with its grid, axis and control arguments marshalled
+    once, for a control loop that filters a few host states per call: each
+    call only copies the states in and the controls out."""
+
+    def __init__(self, grids, axes, ctrl_index, state_dim: int, ctrl_dim: int,
+                 max_states: int = 1):
+        hs = [g.handle if hasattr(g, "handle") else g for g in grids]
+        self._k = len(hs)
+        self._h = (_vp * self._k)(*hs)
+        ax = np.zeros((self._k, HJ_MAX_DIM), dtype=np.int32)
+        for i, a in enumerate(axes):
+            ax[i, :len(a)] = a
+        self._ax = ax
+        self._axp = ax.ctypes.data_as(_P(_i))
+        self._ci = np.ascontiguousarray(ctrl_index, dtype=np.int32)
+        self._cip = self._ci.ctypes.data_as(_P(_i))
+        self._sd, self._cd = int(state_dim), int(ctrl_dim)
+        self._u = np.empty((max_states, ctrl_dim), dtype=np.float64)
+        self._w = np.empty(max_states, dtype=np.float64)
+        self._a = np.empty(max_states, dtype=np.int32)
+        self._fn = lib().hj_safety_filter
+
+    def __call__(self, states: np.ndarray, u_perf: np.ndarray, level: float = 0.0):
+        """states (nq, state_dim), u_perf (nq, ctrl_dim): C-contiguous float64
+        host arrays with nq <= max_states.  Returns views (u, w, active) of
+        buffers that the next call overwrites."""
+        nq = states.shape[0]
+        if nq > self._w.shape[0]:
+            raise ValueError("more states than max_states")
+        rc = self._fn(self._h, self._k, self._axp, self._cip, self._sd, self._cd, nq,
+                      states.ctypes.data, u_perf.ctypes.data, float(level),
+                      self._u.ctypes.data, self._w.ctypes.data, self._a.ctypes.data, 0)
+        if rc != HJ_OK:
+            raise HJError(rc, hj_last_error())
+        return self._u[:nq], self._w[:nq], self._a[:nq]
+
+
 def hj_autotune(g: int, scheme: int = HJ_WENO5) -> int:
     t = ctypes.c_int()
     _check(lib().hj_autotune(g, int(scheme), ctypes.byref(t)))

@@ -337,12 +337,13 @@ def safety_filter(n4: int = 41, n2: int = 201, batch: int = 1 << 20, reps: int =
     dt_batch = (time.perf_counter() - t0) / reps
     active = float((act != 0).float().mean().item())
     one_x, one_u = states[:1].copy(), up[:1].copy()
-    hj.hj_safety_filter(grids, wl.QUAD10D_AXES, wl.QUAD10D_CTRL, one_x, one_u, 0.0)
+    filt = hj.SafetyFilter(grids, wl.QUAD10D_AXES, wl.QUAD10D_CTRL, 10, 3)
+    filt(one_x, one_u, 0.0)
     lat = []
     for i in range(single):
         one_x[0] = states[i]
         t1 = time.perf_counter()
-        hj.hj_safety_filter(grids, wl.QUAD10D_AXES, wl.QUAD10D_CTRL, one_x, one_u, 0.0)
+        filt(one_x, one_u, 0.0)
         lat.append(time.perf_counter() - t1)
     for g in grids:
         g.close()

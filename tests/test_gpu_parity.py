@@ -229,6 +229,10 @@ def test_safety_filter_parity(hj):
     u0, w0, a0 = hj.hj_safety_filter(grids, wl.QUAD10D_AXES, wl.QUAD10D_CTRL, states, up, 0.0)
     assert np.array_equal(ud.cpu().numpy(), u0) and np.array_equal(wd.cpu().numpy(), w0)
     assert np.array_equal(ad.cpu().numpy(), a0)
+    # the prepared filter object gives the same result, state by state
+    filt = hj.SafetyFilter(grids, wl.QUAD10D_AXES, wl.QUAD10D_CTRL, 10, 3, max_states=4)
+    uf, wf, af = filt(np.ascontiguousarray(states[:4]), np.ascontiguousarray(up[:4]), 0.0)
+    assert np.array_equal(uf, u0[:4]) and np.array_equal(wf, w0[:4]) and np.array_equal(af, a0[:4])
     # errors: a state outside a box, a control driven twice
     bad = states[:4].copy()
     bad[0, 0] = 100.0
