@@ -322,6 +322,20 @@ def test_safety_control_brakes_toward_the_safe_set():
     assert u[:, 0].tolist() == [wl.X4_PARAMS[4], wl.X4_PARAMS[5]]
 
 
+def test_safety_filter_tie_keeps_the_clipped_performance_control():
+    """Where the gradient along the input's axis is exactly zero (a value
+    field constant along v), the performance control stays, clipped to the
+    input box."""
+    z = wl.quad_z(21, 0.5)
+    zz = z.coords()[0]
+    W = np.repeat((zz - 1.5)[:, None], 21, axis=1)  # W depends on z only
+    S = np.array([[1.2, 0.4], [1.7, -0.3], [0.9, 0.0]])
+    up = np.array([[25.0], [-3.0], [7.5]])
+    u, w, act = oracle.safety_filter([z], [W], [(0, 1)], [0], S, up, level=10.0)
+    assert act.tolist() == [1, 1, 1]
+    assert u[:, 0].tolist() == [wl.Z_PARAMS[3], wl.Z_PARAMS[2], 7.5]
+
+
 def test_safety_filter_switch_and_decomposed_value():
     """W = min over subsystems; the performance control passes where every
     W_k is above the level; each subsystem drives only its own input."""
@@ -360,6 +374,27 @@ def test_translation_on_the_grid_is_an_index_shift():
             moved[:k] = W0[-k:]
         ref = np.minimum(np.where(np.isinf(moved), l1, moved), l1)
         assert np.abs(P - ref).max() < 1e-12
+
+
+def test_translation_off_the_grid_is_linear_interpolation():
+    """A move by a fraction of a cell reads the source by multilinear
+    interpolation: the same as SciPy's linear grid interpolator at x - s,
+    with the target's l where x - s leaves the source box, then min with l."""
+    from scipy.interpolate import RegularGridInterpolator
+    src = wl.quad_z(41, 0.5, (0.5, 2.5))
+    dst = wl.quad_z(57, 0.5, (0.73, 2.73))
+    Ws = oracle.margin(src) + wl.seeded_field(src, 9, 0.05)
+    shift = (0.23, 0.0)
+    P = oracle.translate(src, Ws, dst, shift)
+    X = np.stack(np.meshgrid(*dst.coords(), indexing="ij"), axis=-1).reshape(-1, 2)
+    Y = X - np.array(shift)
+    inside = np.all((Y >= np.array(src.lo) - 1e-9) & (Y <= np.array(src.hi) + 1e-9), axis=1)
+    f = RegularGridInterpolator(src.coords(), Ws, method="linear")
+    ld = oracle.margin(dst).ravel()
+    ref = ld.copy()
+    ref[inside] = np.minimum(f(np.clip(Y[inside], src.lo, src.hi)), ld[inside])
+    assert np.abs(P.ravel() - ref).max() < 1e-12
+    assert (~inside).any() and inside.any()
 
 
 def test_translated_prior_warm_start_is_exact():
