@@ -524,12 +524,27 @@ def test_x_and_y_identical_inputs_identical_results(hj):
 # ------------------------------------------------------------ full sizes
 
 def test_config1_full_size_fixed_horizon(hj):
-    """41^4, WENO5, five steps from the cold start, in the bench's launch shape."""
+    """41^4, WENO5, five steps from the cold start, with the kernels the
+    bench times: the stage kernels specialised to the 41^4 grid (their
+    background compile is started and awaited first), and the precompiled
+    ones."""
     spec = wl.config1()
     dt = oracle.cfl_dt(spec)
     Wo, _ = oracle.solve(spec, scheme=5, dt=dt, fixed_steps=5)
+    gpu_fixed(hj, spec, 5, 1, dt=dt)
+    assert hj.hj_jit_wait(120.0)
+    before = hj.hj_jit_kernels()
+    launches = hj.hj_kernel_launches()
     Wg, _ = gpu_fixed(hj, spec, 5, 5, dt=dt)
+    assert hj.hj_kernel_launches() > launches
+    assert hj.hj_jit_kernels() >= before and hj.hj_jit_kernels() > 0
     assert_parity(Wg, Wo, spec)
+    try:
+        hj.hj_set_jit(False)
+        Wp, _ = gpu_fixed(hj, spec, 5, 5, dt=dt)
+    finally:
+        hj.hj_set_jit(True)
+    assert np.array_equal(Wg, Wp)
 
 
 def test_config2_batch_full_size_fixed_horizon(hj):
