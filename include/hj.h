@@ -211,7 +211,7 @@ hj_status hj_translate(hj_grid src, hj_grid dst, const double* shift);
  *   - HJ_COLD starts from l.
  *   - HJ_WARM starts from min(prior, l) (Sec. III-B).  The prior is the
  *     grid's current W: the last result, the last hj_set_value, or the last
- *     hj_prolong into this grid.
+ *     hj_prolong or hj_translate into this grid.
  * o may be NULL, which means the defaults.  s may be NULL.
  * On HJ_OK or HJ_ERR_NOT_CONVERGED the grid's W holds the result.
  * Returns:
@@ -221,8 +221,10 @@ hj_status hj_translate(hj_grid src, hj_grid dst, const double* shift);
 hj_status hj_solve(hj_grid g, int mode, const hj_solve_opts* o, hj_solve_stats* s);
 
 /* Solve several grids together (Sec. III-A: decomposed subsystems are
- * independent).  Each time step of all still-unconverged grids is one fused
- * launch per RK stage; each grid keeps its own dt and stop test.  All grids
+ * independent).  In each time step of all still-unconverged grids, the
+ * grids of one kind (model, ndim, scheme) below 2^20 nodes share one fused
+ * launch per RK stage, and larger grids get their own; each grid keeps its
+ * own dt and stop test.  All grids
  * must be on the same device.  The work runs on the stream of gs[0].  modes,
  * opts and stats are arrays of ngrids entries.  opts may be NULL, or point to
  * a single entry when opts_count is 1.  Returns the first non-OK status, in
