@@ -40,3 +40,17 @@ def test_workload_constants_follow_the_paper():
     assert d0 == c["quad10d_d0"]["value"]
     assert d1 == c["quad10d_d1"]["value"]
     assert n0 == c["quad10d_n0"]["value"]
+
+
+def test_serving_trace_matches_the_committed_trace():
+    """The seeded serving trace (the serving workload) is the one committed
+    under tests/golden/ (written by make_serving_trace.py)."""
+    import json
+    import os
+    import sys
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    sys.path.insert(0, here)
+    import make_serving_trace
+    stored = json.load(open(os.path.join(here, "serving_trace_c4.json")))["requests"]
+    assert make_serving_trace.trace_records() == stored
+    assert len(stored) == 256 and stored[-1]["arrival_s"] > 10.0
