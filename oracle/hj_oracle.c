@@ -29,7 +29,7 @@
  *
  * The paper names no numerical scheme.  The discrete operator below is the
  * textbook one (Osher & Fedkiw 2003, Sec. 3.3-3.4 and 5.3; Jiang & Peng 2000;
- * Shu & Osher 1988) with these readings, all stated in the design doc:
+ * Shu & Osher 1988) with these readings, where the paper is silent:
  *   - first-order upwind, ENO2 or WENO5 one-sided differences per axis;
  *   - ghost nodes by linear extrapolation from the two outermost nodes;
  *   - global Lax-Friedrichs: L(W) = H(x, (p-+p+)/2) + sum_i a_i (p+_i - p-_i)/2
