@@ -132,6 +132,23 @@ def test_hamiltonian_max_min_order():
         1.0 + 10.0 * math.pi / 9.0)
 
 
+def test_hamiltonian_asymmetric_input_boxes_x4():
+    """x subsystem with asymmetric control and disturbance boxes: the sign
+    with which u enters dw/dt decides H (with a symmetric box it would not).
+    H = p0 v + p1 g tan(th) + p2 (-d1 th + w) + p3 (-d0 th)
+        + max_u p3 n0 u + min_d p0 d."""
+    import dataclasses
+    x = dataclasses.replace(wl.quad_x4(5, 0.5), params=(9.81, 8.0, 10.0, 10.0, -0.1, 0.3, 0.0),
+                            d_lo=(-0.2,), d_hi=(0.6,))
+    st = [0.0, 0.0, 0.2, 0.0]
+    assert oracle.hamiltonian(x, st, [0, 0, 0, 1.0]) == pytest.approx(-2.0 + 10.0 * 0.3)
+    assert oracle.hamiltonian(x, st, [0, 0, 0, -1.0]) == pytest.approx(2.0 + 10.0 * 0.1)
+    # disturbance on dx/dt: min over [-0.2, 0.6] of p0 d
+    st2 = [0.0, 0.5, 0.0, 0.0]
+    assert oracle.hamiltonian(x, st2, [1.0, 0, 0, 0]) == pytest.approx(0.5 - 0.2)
+    assert oracle.hamiltonian(x, st2, [-1.0, 0, 0, 0]) == pytest.approx(-0.5 - 0.6)
+
+
 # ------------------------------------------------------------- closed forms
 
 @pytest.mark.parametrize("scheme", [2, 5])
@@ -517,6 +534,18 @@ def test_band_stop_test_reduces_to_full_test_and_never_stops_later():
     Wc, _ = oracle.solve(s, scheme=2, tol=1e-8, max_steps=50000)
     near = np.abs(Wc) < 0.25
     assert np.abs(Wn - Wc)[near].max() < 5e-3
+
+
+def test_band_stop_test_stops_where_only_the_faces_still_move():
+    """On a truncated 4-D grid the iterate keeps moving at the faces where
+    trajectories leave the grid; the band test, which watches only
+    |W| <= band around the zero level set, stops long before the full-grid
+    test does."""
+    s = wl.quad_x4(11, 0.8, 4.0, shift=0.5)
+    Wb, stb = oracle.solve(s, scheme=5, tol=1e-4, clamp=1, band=0.5, max_steps=4000)
+    assert stb["converged"] and stb["steps"] < 2500
+    Wf, stf = oracle.solve(s, scheme=5, tol=1e-4, clamp=1, band=0.0, max_steps=4000)
+    assert not stf["converged"] and stf["steps"] == 4000
 
 
 def test_band_margin_skips_faces_of_free_axes_only():
