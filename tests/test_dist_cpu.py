@@ -8,7 +8,6 @@ import multiprocessing as mp
 import os
 import socket
 
-import pytest
 
 
 def _free_port():

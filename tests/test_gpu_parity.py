@@ -7,7 +7,6 @@ Fixed-horizon cases give both sides the same dt and the same step count.
 Converged 2-D cases run the oracle to a 1e-7 window residual and the GPU to
 1e-5, its FP32 floor; converged 4-D cases use the 1e-4 stop rule on both sides.
 """
-import math
 
 import numpy as np
 import pytest
