@@ -3,8 +3,10 @@
 Plants one plausible mistake at a time in a copy of hj_oracle.c (a flipped
 sign, a swapped weight, a dropped term or option), compiles the copy into a
 temporary directory, and runs the CPU pins against it through
-HJ_ORACLE_LIB.  Every mistake must fail at least one pin.  The committed
-source is never modified.
+HJ_ORACLE_LIB.  The oracle's Python parts (translation, safety filter) get
+the same treatment through a modified copy of the package placed first on
+the import path.  Every mistake must fail at least one pin.  The committed
+sources are never modified.
 
     python oracle/mutation_check.py
 """
@@ -64,10 +66,45 @@ MUTATIONS = [
 ]
 
 
+# the same for binding.py
+PY_MUTATIONS = [
+    ("translation reads the source at x + s",
+     [("Y = X - np.asarray(shift, dtype=np.float64)[None, :]",
+       "Y = X + np.asarray(shift, dtype=np.float64)[None, :]")]),
+    ("translated prior not clamped by l",
+     [("out[inside] = np.minimum(query_value(src, Ws, Y[inside]), l[inside])",
+       "out[inside] = query_value(src, Ws, Y[inside])")]),
+    ("z control gain on the wrong axis", [("b[1] = spec.params[0]", "b[0] = spec.params[0]")]),
+    ("x control gain on the wrong axis", [("b[3] = spec.params[3]", "b[2] = spec.params[3]")]),
+    ("decomposed value is the maximum", [("w = np.minimum(w, wk)", "w = np.maximum(w, wk)")]),
+    ("filter switches above the level", [("on = wk <= level", "on = wk >= level")]),
+    ("bang-bang bounds swapped",
+     [("us = np.where(s > 0, uhi, np.where(s < 0, ulo,", "us = np.where(s > 0, ulo, np.where(s < 0, uhi,")]),
+]
+
+
+def _run_pins(env, cwd) -> str:
+    """Runs the pins; returns the first failing test, or '' when all pass.
+    cwd is a scratch directory: `python -m pytest` puts its working
+    directory first on sys.path, which must not hold the real oracle when a
+    modified copy is to be imported."""
+    r = subprocess.run([sys.executable, "-m", "pytest", *[os.path.join(ROOT, p) for p in PINS],
+                        "-q", "-x", "-m", "not gpu", "-p", "no:cacheprovider"], cwd=cwd, env=env,
+                       capture_output=True, text=True)
+    if r.returncode == 0:
+        return ""
+    failed = [l.split("::", 1)[1] for l in r.stdout.splitlines() if l.startswith("FAILED")]
+    return failed[0].split(" ")[0] if failed else "(error)"
+
+
 def main() -> int:
     src = open(os.path.join(HERE, "hj_oracle.c")).read()
     survived = 0
     with tempfile.TemporaryDirectory() as tmp:
+        # a built copy of the unmodified library for the Python mutations
+        base_so = os.path.join(tmp, "base.so")
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                               "-o", base_so, os.path.join(HERE, "hj_oracle.c"), "-lm"])
         for k, (name, edits) in enumerate(MUTATIONS):
             text = src
             for a, b in edits:
@@ -79,17 +116,33 @@ def main() -> int:
             open(c, "w").write(text)
             subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
                                    "-o", so, c, "-lm"])
-            env = dict(os.environ, HJ_ORACLE_LIB=so)
-            r = subprocess.run([sys.executable, "-m", "pytest", *PINS, "-q", "-x", "-m", "not gpu",
-                                "-p", "no:cacheprovider"], cwd=ROOT, env=env,
-                               capture_output=True, text=True)
-            failed = [l.split("::", 1)[1] for l in r.stdout.splitlines() if l.startswith("FAILED")]
-            if r.returncode == 0:
+            first = _run_pins(dict(os.environ, HJ_ORACLE_LIB=so), tmp)
+            if not first:
                 survived += 1
                 print("SURVIVED  %s" % name)
             else:
-                print("caught    %-48s by %s" % (name, failed[0].split(" ")[0] if failed else "?"))
-    print("%d of %d mistakes caught" % (len(MUTATIONS) - survived, len(MUTATIONS)))
+                print("caught    %-48s by %s" % (name, first))
+        binding = open(os.path.join(HERE, "binding.py")).read()
+        for k, (name, edits) in enumerate(PY_MUTATIONS):
+            text = binding
+            for a, b in edits:
+                if a not in text:
+                    raise SystemExit("mutation %r: pattern not found" % name)
+                text = text.replace(a, b, 1)
+            pkg = os.path.join(tmp, "py%d" % k, "oracle")
+            os.makedirs(pkg)
+            open(os.path.join(pkg, "binding.py"), "w").write(text)
+            open(os.path.join(pkg, "__init__.py"), "w").write(
+                open(os.path.join(HERE, "__init__.py")).read())
+            path = os.pathsep.join([os.path.dirname(pkg), ROOT, os.environ.get("PYTHONPATH", "")])
+            first = _run_pins(dict(os.environ, HJ_ORACLE_LIB=base_so, PYTHONPATH=path), tmp)
+            if not first:
+                survived += 1
+                print("SURVIVED  %s" % name)
+            else:
+                print("caught    %-48s by %s" % (name, first))
+    total = len(MUTATIONS) + len(PY_MUTATIONS)
+    print("%d of %d mistakes caught" % (total - survived, total))
     return 1 if survived else 0
 
 

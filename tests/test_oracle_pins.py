@@ -339,6 +339,28 @@ def test_safety_control_brakes_toward_the_safe_set():
     assert u[:, 0].tolist() == [wl.X4_PARAMS[4], wl.X4_PARAMS[5]]
 
 
+@pytest.mark.parametrize("make", [lambda: wl.quad_z(11, 0.5), lambda: wl.quad_x4(5, 0.5)])
+def test_control_gain_matches_the_model(make):
+    """The filter's df/du (per axis) agrees with the model that H is built
+    on: raising the input's upper bound by du changes H(x, e_k) only on the
+    controlled axis k, and there by gain_k du."""
+    import dataclasses
+    spec = make()
+    b, ulo, uhi = oracle.control_gain(spec)
+    iu = 3 if spec.model == wl.QUAD_Z else 5   # index of u_hi in the model parameters
+    du = 0.25
+    params = list(spec.params)
+    params[iu] += du
+    raised = dataclasses.replace(spec, params=tuple(params))
+    x = [0.3, 0.2, 0.1, 0.05][:spec.ndim]
+    for k in range(spec.ndim):
+        e = [0.0] * spec.ndim
+        e[k] = 1.0
+        dH = oracle.hamiltonian(raised, x, e) - oracle.hamiltonian(spec, x, e)
+        assert dH == pytest.approx(b[k] * du, abs=1e-12)
+    assert b.any() and uhi == spec.params[iu]
+
+
 def test_safety_filter_tie_keeps_the_clipped_performance_control():
     """Where the gradient along the input's axis is exactly zero (a value
     field constant along v), the performance control stays, clipped to the
