@@ -471,6 +471,12 @@ hj_status hj_autotune(hj_grid g, int scheme, int* threads_out);
 void hj_set_jit(int enable);
 long long hj_jit_kernels(void);
 long long hj_jit_pending(void);
+/* Diagnostic: builds the shape-specialised stage source for an ndim grid of
+ * n[i] nodes per axis, the model and the scheme, and compiles it with NVRTC
+ * for sm_103a.  Needs no device.  HJ_ERR_ARG on bad arguments; HJ_ERR_CUDA
+ * when NVRTC is missing or the compile fails (hj_last_error holds the start
+ * of NVRTC's log). */
+hj_status hj_jit_check(int ndim, const int* n, int model, int scheme, int threads);
 
 /* Number of nodes of the grid. */
 long long hj_grid_points(hj_grid g);

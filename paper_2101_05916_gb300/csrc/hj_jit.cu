@@ -26,6 +26,8 @@
 #include <thread>
 #include <vector>
 
+#include "hj.h"
+#include "hj_grid.h"
 #include "hj_internal.h"
 
 // kJitHeaderNames / kJitHeaders: the device headers as text (build.py)
@@ -190,8 +192,9 @@ std::string source(const hjd::DevGrid& g, int scheme, int threads) {
   return s;
 }
 
-// NVRTC compile of one kernel set (no CUDA calls).
-std::vector<char> compile(const std::string& src) {
+// NVRTC compile of one kernel set (no CUDA calls).  *log, when given,
+// receives NVRTC's log.
+std::vector<char> compile(const std::string& src, std::string* log = nullptr) {
   std::vector<char> cubin;
   const Nvrtc& n = nvrtc();
   if (!n.ok) return cubin;
@@ -202,8 +205,15 @@ std::vector<char> compile(const std::string& src) {
     return cubin;
   const char* opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-ftz=true", "-lineinfo"};
   size_t sz = 0;
-  if (n.compile(prog, 4, opts) == NVRTC_SUCCESS && n.cubin_size(prog, &sz) == NVRTC_SUCCESS &&
-      sz > 0) {
+  nvrtcResult rc = n.compile(prog, 4, opts);
+  if (log) {
+    size_t ls = 0;
+    if (n.log_size(prog, &ls) == NVRTC_SUCCESS && ls > 1) {
+      std::vector<char> buf(ls);
+      if (n.log(prog, buf.data()) == NVRTC_SUCCESS) log->assign(buf.data());
+    }
+  }
+  if (rc == NVRTC_SUCCESS && n.cubin_size(prog, &sz) == NVRTC_SUCCESS && sz > 0) {
     cubin.resize(sz);
     if (n.cubin(prog, cubin.data()) != NVRTC_SUCCESS) cubin.clear();
   }
@@ -346,3 +356,38 @@ long long jit_pending() { return g_pending.load(); }
 void jit_enable(int on) { g_enabled.store(on ? 1 : 0); }
 
 }  // namespace hjk
+
+extern "C" hj_status hj_jit_check(int ndim, const int* n, int model, int scheme, int threads) {
+  if (ndim < 1 || ndim > HJ_MAX_DIM || !n) return hja::fail(HJ_ERR_ARG, "bad grid shape");
+  if (model != HJ_DRIFT && model != HJ_QUAD_Z && model != HJ_QUAD_X4)
+    return hja::fail(HJ_ERR_ARG, "unknown model %d", model);
+  if (scheme != HJ_FIRST && scheme != HJ_ENO2 && scheme != HJ_WENO5)
+    return hja::fail(HJ_ERR_ARG, "unknown scheme %d", scheme);
+  if (threads != 128 && threads != 256 && threads != 512)
+    return hja::fail(HJ_ERR_ARG, "threads must be 128, 256 or 512");
+  // a grid description on the stack over [0, 1]^ndim with a box constraint:
+  // enough for the descriptor; no device memory is touched
+  hj_grid_s g;
+  g.ndim = ndim;
+  long long npts = 1;
+  for (int i = 0; i < ndim; ++i) {
+    if (n[i] < 3) return hja::fail(HJ_ERR_ARG, "axis %d has fewer than 3 nodes", i);
+    g.n[i] = n[i];
+    g.lo[i] = 0.0;
+    g.hi[i] = 1.0;
+    g.h[i] = 1.0 / (double)(n[i] - 1);
+    g.ca[i] = 0.25;
+    g.cb[i] = 0.75;
+    npts *= n[i];
+  }
+  if (npts >= (1ll << 31)) return hja::fail(HJ_ERR_ARG, "grid too large");
+  g.npts = npts;
+  g.model = model;
+  g.con_kind = hjd::C_BOX;
+  hjd::DevGrid d = hja::devgrid(&g);
+  if (!hjk::nvrtc().ok) return hja::fail(HJ_ERR_CUDA, "NVRTC could not be loaded");
+  std::string log;
+  std::vector<char> cubin = hjk::compile(hjk::source(d, scheme, threads), &log);
+  if (cubin.empty()) return hja::fail(HJ_ERR_CUDA, "NVRTC: %.400s", log.c_str());
+  return HJ_OK;
+}

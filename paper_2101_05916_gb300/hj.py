@@ -103,6 +103,7 @@ SIGNATURES = {
     "hj_set_jit": (None, [_i]),
     "hj_jit_kernels": (_ll, []),
     "hj_jit_pending": (_ll, []),
+    "hj_jit_check": (_i, [_i, _P(_i), _i, _i, _i]),
     "hj_set_value": (_i, [_vp, _vp, _i]),
     "hj_get_value": (_i, [_vp, _vp, _i]),
     "hj_query_value": (_i, [_vp, _i, _P(_d), _P(_d)]),
@@ -403,6 +404,14 @@ def hj_jit_kernels() -> int:
 
 def hj_jit_pending() -> int:
     return int(lib().hj_jit_pending())
+
+
+def hj_jit_check(n: Sequence[int], model, scheme: int, threads: int = 256) -> None:
+    """Compile the shape-specialised stage source for this grid shape, model
+    and scheme with NVRTC (no device needed); raises HJError on failure."""
+    m = MODELS[model] if isinstance(model, str) else int(model)
+    arr = (_i * len(n))(*[int(v) for v in n])
+    _check(lib().hj_jit_check(len(n), arr, m, int(scheme), int(threads)))
 
 
 def hj_jit_wait(timeout_s: float = 120.0) -> bool:
