@@ -377,8 +377,8 @@ static void lf_rhs(const or_problem* P, int scheme, const double* alpha,
   int r = (scheme == 5) ? 3 : (scheme == 2) ? 2 : 1;
 #pragma omp parallel for schedule(static)
   for (long pt = 0; pt < npts; ++pt) {
-    long idx[OR_MAXD];
-    double x[OR_MAXD], pm[OR_MAXD], pp[OR_MAXD], pbar[OR_MAXD];
+    long idx[OR_MAXD] = {0};
+    double x[OR_MAXD] = {0}, pm[OR_MAXD] = {0}, pp[OR_MAXD] = {0}, pbar[OR_MAXD] = {0};
     grid_unravel(P, pt, idx);
     grid_coords(P, idx, x);
     for (int d = 0; d < P->ndim; ++d) {

@@ -194,9 +194,9 @@ extern "C" hj_status hj_solve_fixed_static(int ndim, const int* n, const double*
   HJ_CU(launch_static_init(d, Wk, mode == HJ_WARM ? 1 : 0, s));
   if (step > 0.0) {
     float fdt = (float)step;
-    hjd::StageArgs a1{Wk, Wk, A, nullptr, nullptr, fdt, 0, clamp, 0.f};
-    hjd::StageArgs a2{A, Wk, B, nullptr, nullptr, fdt, 0, clamp, 0.f};
-    hjd::StageArgs a3{B, Wk, Wk, nullptr, nullptr, fdt, 0, clamp, 0.f};
+    hjd::StageArgs a1{Wk, Wk, A, nullptr, nullptr, fdt, 0, clamp, 0.f, 0};
+    hjd::StageArgs a2{A, Wk, B, nullptr, nullptr, fdt, 0, clamp, 0.f, 0};
+    hjd::StageArgs a3{B, Wk, Wk, nullptr, nullptr, fdt, 0, clamp, 0.f, 0};
     for (long long k = 0; k < steps; ++k) {
       HJ_CU(hjk::launch_stage(d, scheme, 1, a1, s, hjk::kStageThreads, false));
       HJ_CU(hjk::launch_stage(d, scheme, 2, a2, s, hjk::kStageThreads, false));
