@@ -415,7 +415,11 @@ hj_status hj_safety_filter(const hj_grid* grids, int ngrids, const int* axes,
  *   - W is caller-owned device memory with npts = n[0]*..*n[ndim-1] floats.
  *     With HJ_WARM it holds the prior on entry (HJ_COLD ignores it).  On
  *     return it holds the value after `steps` TVD-RK3 steps.
- *   - dt <= 0 selects the CFL step with cfl = 0.5.
+ *   - dt == 0 selects the CFL step with cfl = 0.5; dt < 0 (or NaN) is
+ *     rejected with HJ_ERR_ARG.
+ *   - W must be device (or managed) memory of the current device; a host
+ *     pointer or memory of another device is rejected with HJ_ERR_ARG
+ *     before any device work.
  *   - clamp is HJ_CLAMP_VI or HJ_CLAMP_MONOTONE.
  *   - The call returns after the work on cuda_stream has finished.
  *
@@ -433,7 +437,12 @@ hj_status hj_safety_filter(const hj_grid* grids, int ngrids, const int* axes,
  * routine.
  *
  * First call on a device: it looks up the array's device address with that
- * device current.  Make that first call before any stream capture.
+ * device current.  Under lazy module loading (the CUDA default) that lookup
+ * is also when the driver loads the module on the device and reserves the
+ * 48 MiB array, so the first call can be slow or fail with HJ_ERR_CUDA when
+ * the device is full.  Make one call (any small grid, steps = 0) on each
+ * device at start-up, before any stream capture and before the device's
+ * memory is handed to another pool.
  *
  * Concurrency: the array keeps the contents of the last call.  The call
  * clears what must start at zero itself.  Calls whose GPU work overlaps

@@ -11,7 +11,9 @@
 // never passes the symbol itself to a kernel: on the host that name is only
 // a stand-in, not a device address.  Instead, the first call on each device
 // asks the runtime for the array's device address with that device current,
-// caches it, and hands that pointer to the kernels.
+// caches it, and hands that pointer to the kernels.  Under lazy module
+// loading (the CUDA default) that lookup is also the moment the driver loads
+// this module on the device and reserves the array.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -70,8 +72,7 @@ __global__ void static_init_kernel(const hjd::DevGrid g, float* W, int warm) {
 }
 
 cudaError_t launch_static_init(const hjd::DevGrid& g, float* W, int warm, cudaStream_t s) {
-  int b = (g.npts + 255) / 256;
-  unsigned nb = (unsigned)(b < 152 * 16 ? b : 152 * 16);
+  unsigned nb = hjk::stride_blocks(g.npts, 256);
   switch (g.ndim) {
     case 1: static_init_kernel<1><<<nb, 256, 0, s>>>(g, W, warm); break;
     case 2: static_init_kernel<2><<<nb, 256, 0, s>>>(g, W, warm); break;
@@ -96,6 +97,7 @@ extern "C" hj_status hj_solve_fixed_static(int ndim, const int* n, const double*
     return hja::fail(HJ_ERR_ARG, "bad grid description");
   if (mode != HJ_COLD && mode != HJ_WARM) return hja::fail(HJ_ERR_ARG, "bad mode");
   if (clamp != HJ_CLAMP_VI && clamp != HJ_CLAMP_MONOTONE) return hja::fail(HJ_ERR_ARG, "bad clamp");
+  // dt == 0 selects the CFL step; a negative or NaN dt is an argument error
   if (steps < 0 || !(dt >= 0.0)) return hja::fail(HJ_ERR_ARG, "need steps >= 0 and dt >= 0");
   if (!box_lo || !box_hi) return hja::fail(HJ_ERR_ARG, "box is NULL");
   // A handle on the stack: no allocation, only the description fields are used.
@@ -159,6 +161,18 @@ extern "C" hj_status hj_solve_fixed_static(int ndim, const int* n, const double*
 
   int dev = 0;
   HJ_CU(cudaGetDevice(&dev));
+  // W must be device (or managed) memory of the current device: a host
+  // pointer, or memory of another GPU, would fault inside the kernels.
+  // Asking for its attributes allocates nothing.
+  cudaPointerAttributes pa;
+  std::memset(&pa, 0, sizeof(pa));
+  cudaError_t pe = cudaPointerGetAttributes(&pa, W);
+  if (pe != cudaSuccess) {
+    cudaGetLastError();
+    return hja::fail(HJ_ERR_ARG, "W is not a CUDA pointer: %s", cudaGetErrorString(pe));
+  }
+  if (!(pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged) || pa.device != dev)
+    return hja::fail(HJ_ERR_ARG, "W must be device memory of the current device %d", dev);
   unsigned char* base = nullptr;
   if ((st = scratch_address(dev, &base)) != HJ_OK) return st;
   unsigned* alpha_bits = reinterpret_cast<unsigned*>(base);

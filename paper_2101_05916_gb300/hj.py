@@ -489,6 +489,10 @@ def hj_solve_fixed_static(spec, W, mode: int = HJ_COLD, scheme: int = HJ_WENO5,
     ptr, dev, keep = _field_ptr(W, int(np.prod(spec.n)), True)
     if not dev:
         raise ValueError("W must be device memory")
+    import torch
+    if W.device.index is not None and W.device.index != torch.cuda.current_device():
+        raise ValueError("W lives on cuda:%d but cuda:%d is current"
+                         % (W.device.index, torch.cuda.current_device()))
     _check(lib().hj_solve_fixed_static(nd, na, _darr(spec.lo), _darr(spec.hi), m,
                                        _darr(spec.params), len(spec.params), _darr(spec.d_lo),
                                        _darr(spec.d_hi), len(spec.d_lo), _darr(spec.con_a),

@@ -98,3 +98,42 @@ def test_static_entry_rejects_oversized_grids(hj):
                                  hj._darr(spec.con_b), 0, 5, 0.0, 1, 0, W.data_ptr(), None)
     assert rc == hj.HJ_ERR_ARG
     assert "allocation-free limit" in hj.hj_last_error()
+
+
+def raw_call(hj, spec, ptr, dt=0.0, steps=1, scheme=2):
+    import ctypes
+    n = (ctypes.c_int * spec.ndim)(*[int(v) for v in spec.n])
+    return hj.lib().hj_solve_fixed_static(
+        spec.ndim, n, hj._darr(spec.lo), hj._darr(spec.hi), hj.MODELS[spec.model],
+        hj._darr(spec.params), len(spec.params), hj._darr(spec.d_lo), hj._darr(spec.d_hi),
+        len(spec.d_lo), hj._darr(spec.con_a), hj._darr(spec.con_b), hj.HJ_COLD, scheme,
+        float(dt), int(steps), hj.HJ_CLAMP_VI, ptr, None)
+
+
+def test_static_entry_rejects_host_memory_before_any_launch(hj):
+    """A C caller that hands over a host pointer gets HJ_ERR_ARG, and no kernel
+    runs on that memory."""
+    spec = wl.quad_z(21, 0.5)
+    host = np.zeros(spec.npts, dtype=np.float32)
+    launches = hj.hj_kernel_launches()
+    rc = raw_call(hj, spec, host.ctypes.data)
+    assert rc == hj.HJ_ERR_ARG
+    assert "device memory" in hj.hj_last_error() or "CUDA pointer" in hj.hj_last_error()
+    assert hj.hj_kernel_launches() == launches
+    assert np.all(host == 0.0)
+
+
+def test_static_entry_dt_zero_is_cfl_and_negative_dt_is_rejected(hj):
+    import torch
+    spec = wl.quad_z(41, 0.5)
+    W = torch.zeros(spec.npts, device="cuda", dtype=torch.float32)
+    launches = hj.hj_kernel_launches()
+    assert raw_call(hj, spec, W.data_ptr(), dt=-1e-3) == hj.HJ_ERR_ARG
+    assert raw_call(hj, spec, W.data_ptr(), dt=float("nan")) == hj.HJ_ERR_ARG
+    assert hj.hj_kernel_launches() == launches
+    # dt == 0: the CFL step, the same as the allocating path's default dt
+    assert raw_call(hj, spec, W.data_ptr(), dt=0.0, steps=7) == hj.HJ_OK
+    torch.cuda.synchronize()
+    ref, st = reference(hj, spec, 2, 7, hj.HJ_COLD)
+    assert st["dt"] > 0.0
+    assert close(W.cpu().numpy().reshape(spec.n), ref)
