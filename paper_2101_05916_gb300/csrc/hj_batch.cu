@@ -27,8 +27,9 @@
 namespace hjb {
 
 constexpr int kThreads = hjk::kStageThreads;
-// Grids with at least this many nodes launch alone (about 1.5 waves of the
-// 152 SMs at 8 blocks of 256 threads); smaller grids of one kind are fused.
+// Grids with at least this many nodes launch alone (4096 blocks of 256
+// threads: several waves of a GPU with about 150 SMs at 8 resident blocks
+// each); smaller grids of one kind are fused.
 constexpr int kSoloNodes = 1 << 20;
 
 __host__ __device__ constexpr int kind_code(int model, int ndim, int scheme) {

@@ -15,6 +15,12 @@ extern std::atomic<unsigned long long> g_launches;
 // Threads per block of the stencil kernels.
 constexpr int kStageThreads = 256;
 
+// Streaming multiprocessors of the current device (read once per device).
+int num_sms();
+// Blocks of a grid-stride launch over `work` items: enough to cover them,
+// capped at 16 blocks per SM of the current device.
+unsigned stride_blocks(long long work, int threads);
+
 // One TVD-RK3 stage on one grid.  stage is 1, 2 or 3; scheme 1, 2 or 5;
 // threads per block 128, 256 or 512 (other values use 256).  allow_jit:
 // grids of at least kJitNodes nodes may run the shape-specialised kernel.

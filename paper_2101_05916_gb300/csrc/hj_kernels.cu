@@ -244,11 +244,32 @@ cudaError_t launch_stage(const DevGrid& g, int scheme, int stage, const StageArg
   return cudaErrorInvalidValue;
 }
 
-static unsigned flat_blocks(int npts, int threads) {
-  int b = (npts + threads - 1) / threads;
-  // grid-stride loops: cap at a few waves of the 152 SMs
-  return (unsigned)std::min(b, 152 * 16);
+int num_sms() {
+  static std::atomic<int> cached[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = -1;
+  if (dev >= 0) {
+    int v = cached[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+  }
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev < 0 ? 0 : dev) !=
+          cudaSuccess ||
+      sms <= 0) {
+    cudaGetLastError();
+    sms = 1;
+  }
+  if (dev >= 0) cached[dev].store(sms, std::memory_order_relaxed);
+  return sms;
 }
+
+unsigned stride_blocks(long long work, int threads) {
+  long long b = (work + threads - 1) / threads;
+  // grid-stride loops: cap at a few waves of the device's SMs
+  return (unsigned)std::max(1ll, std::min(b, 16ll * num_sms()));
+}
+
+static unsigned flat_blocks(int npts, int threads) { return stride_blocks(npts, threads); }
 
 cudaError_t launch_alpha(const DevGrid& g, unsigned* out, cudaStream_t s) {
   unsigned nb = flat_blocks(g.npts, 256);
@@ -310,7 +331,7 @@ __global__ void field_check_kernel(const float* __restrict__ lo, const float* __
 cudaError_t launch_field_check(const float* lo, const float* hi, long long n, int* bad,
                                cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  unsigned nb = (unsigned)std::min<long long>((n + 255) / 256, 152 * 16);
+  unsigned nb = stride_blocks(n, 256);
   field_check_kernel<<<nb, 256, 0, s>>>(lo, hi, n, bad);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
