@@ -11,7 +11,7 @@ from __future__ import annotations
 
 import threading
 import time
-from typing import Dict, List, Sequence
+from typing import Dict, List, Optional, Sequence
 
 import numpy as np
 
@@ -44,7 +44,8 @@ def solve_opts_for(req) -> Dict:
 def replay_server(trace: Sequence, budget_bytes: int = 40 << 30, max_active: int = 64,
                   time_scale: float = 1.0, warm: bool = True, stream=None,
                   order: int = hj.HJ_ORDER_SHORTEST, max_active_nodes: int = 6_000_000,
-                  coarse_4d: int = 0, coarse_levels: int = 1, coarse_scheme: int = 0) -> Dict:
+                  coarse_4d: int = 0, coarse_levels: int = 1, coarse_scheme: int = 0,
+                  keep_values: bool = False) -> Dict:
     """Replay `trace` (workloads.Request list); returns latency stats.
 
     Default policy: shortest estimated work first, at most 6M nodes of large
@@ -52,7 +53,9 @@ def replay_server(trace: Sequence, budget_bytes: int = 40 << 30, max_active: int
     4-D request with coarse initialisation (Sec. III-C) on a grid of
     max(coarse_4d, n/2) nodes per axis: exact or conservative, far fewer fine
     steps.  coarse_levels = 2 adds a coarser level of max(9, n/4) nodes below
-    it; coarse_scheme sets the coarse levels' scheme (0: the request's)."""
+    it; coarse_scheme sets the coarse levels' scheme (0: the request's).
+    keep_values: each request's result is copied into a device tensor
+    (returned under "values", in trace order) before its ticket is released."""
     s = hj.hj_server_create(budget_bytes, max_active, stream)
     hj.hj_server_set_policy(s, order, max_active_nodes)
     tickets: List[int] = [0] * len(trace)
@@ -77,12 +80,17 @@ def replay_server(trace: Sequence, budget_bytes: int = 40 << 30, max_active: int
     th = threading.Thread(target=submit)
     th.start()
     th.join()
-    lat, statuses, steps = [], [], []
-    for t in tickets:
+    lat, statuses, steps, values = [], [], [], []
+    for r, t in zip(trace, tickets):
         rc, st = hj.hj_server_wait(s, t)
         statuses.append(rc)
         lat.append(st["wall_ms"])
         steps.append(st["steps"])
+        if keep_values:
+            import torch
+            v = torch.empty(r.spec.npts, dtype=torch.float32, device="cuda")
+            hj.hj_server_get_value(s, t, v)
+            values.append(v)
         hj.hj_server_release(s, t)
     stats = hj.hj_server_get_stats(s)
     hj.hj_server_destroy(s)
@@ -90,31 +98,51 @@ def replay_server(trace: Sequence, budget_bytes: int = 40 << 30, max_active: int
     return dict(p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
                 mean_ms=float(np.mean(lat)), wall_s=wall, statuses=statuses,
                 updates=stats["updates"], updates_per_s=stats["updates"] / max(wall, 1e-9),
-                server=stats, latencies_ms=lat, steps=steps)
+                server=stats, latencies_ms=lat, steps=steps, values=values)
 
 
-def replay_fifo_cold(trace: Sequence, time_scale: float = 1.0, stream=None) -> Dict:
+def replay_fifo_cold(trace: Sequence, time_scale: float = 1.0, stream=None,
+                     check: Optional[Dict[str, List]] = None) -> Dict:
     """The plain baseline: each request solved cold on its own grid, one at a
-    time, in arrival order; latency = completion - arrival."""
+    time, in arrival order; latency = completion - arrival.
+
+    check: {form name: per-request device tensors of another way of serving
+    the same trace}.  Each of them is compared node by node with the cold
+    result of its request (scenarios.accuracy) right after that request's
+    solve, outside the latency clock; the results come back under
+    "accuracy"."""
+    from .scenarios import _acc
     t0 = time.perf_counter()
     lat, updates, statuses = [], 0.0, []
-    for r in trace:
+    acc = {k: [] for k in (check or {})}
+    paused = 0.0
+    for i, r in enumerate(trace):
         arrive = r.arrival_s * time_scale
-        now = time.perf_counter() - t0
+        now = time.perf_counter() - t0 - paused
         if arrive > now:
             time.sleep(arrive - now)
         g = hj.Grid.from_spec(r.spec, stream=stream)
         opts = solve_opts_for(r)
         rc, st = hj.hj_solve(g.handle, hj.HJ_COLD, hj.make_opts(**opts), raise_on_error=False)
+        done = time.perf_counter() - t0 - paused
+        if check:
+            # the comparison is not part of the plain way's latency: its
+            # time is taken off the clock
+            p0 = time.perf_counter()
+            import torch
+            v = torch.empty(r.spec.npts, dtype=torch.float32, device="cuda")
+            g.value_into(v)
+            for name, vals in check.items():
+                acc[name].append(_acc(vals[i].reshape(r.spec.n), v.reshape(r.spec.n), r.spec))
+            paused += time.perf_counter() - p0
         g.close()
-        done = time.perf_counter() - t0
         lat.append(1e3 * (done - arrive))
         updates += float(r.spec.npts) * st["steps"]
         statuses.append(rc)
-    wall = time.perf_counter() - t0
+    wall = time.perf_counter() - t0 - paused
     return dict(p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
                 mean_ms=float(np.mean(lat)), wall_s=wall, statuses=statuses, updates=updates,
-                updates_per_s=updates / max(wall, 1e-9), latencies_ms=lat)
+                updates_per_s=updates / max(wall, 1e-9), latencies_ms=lat, accuracy=acc)
 
 
 def main(argv=None) -> None:
