@@ -102,11 +102,24 @@ typedef struct {
                          /* min(|W|, |W_window_start|) <= band, i.e. the band around the  */
                          /* zero level set that bounds the safe set (Sec. II-A).          */
                          /* 0 (default): every node.                                      */
-  int autotune;          /* 1: pick the stage-kernel block size by timing (hj_autotune)   */
+  int autotune;          /* 1: pick the stage kernels' launch shape by timing (hj_autotune) */
                          /* once per grid shape before solving (default 0)                */
   int band_margin;       /* the stop test skips nodes closer than this many cells to a    */
                          /* face of an unconstrained axis (every axis for a ball), where  */
                          /* trajectories leave a truncated grid (default 0)               */
+  double local_tol;      /* > 0: localized stepping (Sec. VI): after the first window,    */
+                         /* only slabs whose value changed by more than local_tol in the  */
+                         /* last window (nodes within band_margin of a free face do not   */
+                         /* count; nodes outside the band do), and slabs within           */
+                         /* local_margin of them, step;                                   */
+                         /* the others keep their value.  Slabs are the lines of the two  */
+                         /* slowest axes of a 4-D grid, the first axis of a 2-D or 3-D    */
+                         /* grid.  Stage values next to stepping slabs are recomputed on  */
+                         /* rings of 1 and 2 stencil radii, so that every stepping node's */
+                         /* update is the full solve's update of the current field.       */
+                         /* Needs row tiles (the launch shape is switched to them if      */
+                         /* needed); ignored with fixed_steps.  0 (default): off.         */
+  int local_margin;      /* reactivation margin in slabs (default 2)                      */
 } hj_solve_opts;
 
 typedef struct {
@@ -117,6 +130,8 @@ typedef struct {
   double wall_ms;    /* host wall time of the call                            */
   int converged;     /* 1 if residual < tol                                   */
   long long windows; /* stop tests performed                                  */
+  double stepped;    /* stage-kernel tiles run / tiles of full stepping (1 unless */
+                     /* localized)                                               */
 } hj_solve_stats;
 
 /* Fill *o with the defaults listed above. */
@@ -457,14 +472,32 @@ hj_status hj_solve_fixed_static(int ndim, const int* n, const double* lo, const 
                                 int scheme, double dt, long long steps, int clamp, float* W,
                                 void* cuda_stream);
 
-/* Launch-shape autotuner.  It picks the stage kernel's threads per block
- * (128, 256 or 512) for this grid and scheme.  It times a few TVD-RK3 steps
- * of each candidate on the grid's current value, or on l if the grid holds
- * none, and keeps the fastest.  W is left unchanged.  The choice is cached
- * per (model, ndim, scheme, grid shape) for the whole process, and later
- * solves of this grid use it.  *threads_out (may be NULL) receives the
- * choice. */
+/* Launch-shape autotuner.  It picks how the stage kernels map onto the
+ * GPU for this grid and scheme, among:
+ *   - the flat mapping: one thread per node over the flattened grid, in
+ *     blocks of 128, 256 or 512 threads;
+ *   - row tiles: each block stages tile_rows consecutive lines of the
+ *     fastest axis in shared memory (16-byte loads, ghost values in place)
+ *     and computes their nodes; the candidates are the line counts whose
+ *     blocks (128 to 1024 threads) fill their warps best.  The halo width
+ *     of a tile is the scheme's stencil radius (3 for WENO5, 2 for ENO2).
+ * Every shape computes the same values bit for bit.  It times a few
+ * TVD-RK3 steps of each candidate on the grid's current value, or on l if
+ * the grid holds none (with the shape-specialised kernels where the grid
+ * uses them), and keeps the fastest.  W is left unchanged.  The choice is
+ * cached per (model, ndim, scheme, grid shape) for the whole process, and
+ * later solves of this grid use it.  *threads_out (may be NULL) receives
+ * the flat block size; hj_get_launch_shape gives the whole choice. */
 hj_status hj_autotune(hj_grid g, int scheme, int* threads_out);
+
+/* Sets the stage kernels' launch shape by hand: threads per block of the
+ * flat mapping (128, 256 or 512) and tile_rows (0: the flat mapping; > 0:
+ * row tiles of that many fastest-axis lines, at most 1024 nodes per tile).
+ * HJ_ERR_ARG when the tile does not fit the grid.  Results do not depend on
+ * the shape. */
+hj_status hj_set_launch_shape(hj_grid g, int threads, int tile_rows);
+/* The current launch shape (either pointer may be NULL). */
+hj_status hj_get_launch_shape(hj_grid g, int* threads, int* tile_rows);
 
 /* Shape-specialised stage kernels.  For grids of at least 2^20 nodes the
  * library compiles at run time (NVRTC, from the first use per grid shape,
@@ -486,6 +519,8 @@ long long hj_jit_pending(void);
  * when NVRTC is missing or the compile fails (hj_last_error holds the start
  * of NVRTC's log). */
 hj_status hj_jit_check(int ndim, const int* n, int model, int scheme, int threads);
+/* The same for the row-tile stage kernels of tile_rows lines per block. */
+hj_status hj_jit_check_tiles(int ndim, const int* n, int model, int scheme, int tile_rows);
 
 /* Number of nodes of the grid. */
 long long hj_grid_points(hj_grid g);

@@ -19,6 +19,8 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
+#include <vector>
 
 #include "hj_grid.h"
 
@@ -46,8 +48,10 @@ hjd::DevGrid devgrid(const hj_grid g) {
   }
   d.npts = (int)g->npts;
   d.plane = g->ndim == 4 ? (int)(g->npts / g->n[0]) : (int)g->npts;
-  // multiply-shift reciprocals of the two fastest axis lengths (see fast_div)
-  for (int k = 0; k < 2; ++k) {
+  d.nrows = (int)(g->npts / g->n[g->ndim - 1]);
+  d.tile_rows = g->tile_rows;
+  // multiply-shift reciprocals of the three fastest axis lengths (see fast_div)
+  for (int k = 0; k < 3; ++k) {
     int ax = g->ndim - 1 - k;
     unsigned dv = ax >= 0 ? (unsigned)g->n[ax] : 2u;
     int l = 0;
@@ -146,17 +150,17 @@ static void invalidate(hj_grid g) {
 // k TVD-RK3 steps; the last one folds the window residual when check_last.
 static cudaError_t enqueue_steps(hj_grid g, const hjd::DevGrid& d, int scheme, int clamp,
                                  float band, int margin, float dt, long long k, bool check_last,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, bool allow_jit = true) {
   hjd::StageArgs a1{g->W, g->W, g->A, nullptr, nullptr, dt, 0, clamp, band, margin};
   hjd::StageArgs a2{g->A, g->W, g->B, nullptr, nullptr, dt, 0, clamp, band, margin};
   hjd::StageArgs a3{g->B, g->W, g->W, g->snap, g->dscal + 4, dt, 0, clamp, band, margin};
   const int t = g->threads;
   for (long long i = 0; i < k; ++i) {
     cudaError_t e;
-    if ((e = hjk::launch_stage(d, scheme, 1, a1, s, t)) != cudaSuccess) return e;
-    if ((e = hjk::launch_stage(d, scheme, 2, a2, s, t)) != cudaSuccess) return e;
+    if ((e = hjk::launch_stage(d, scheme, 1, a1, s, t, allow_jit)) != cudaSuccess) return e;
+    if ((e = hjk::launch_stage(d, scheme, 2, a2, s, t, allow_jit)) != cudaSuccess) return e;
     a3.check = (check_last && i == k - 1) ? 1 : 0;
-    if ((e = hjk::launch_stage(d, scheme, 3, a3, s, t)) != cudaSuccess) return e;
+    if ((e = hjk::launch_stage(d, scheme, 3, a3, s, t, allow_jit)) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
@@ -179,7 +183,7 @@ static hj_status run_window(hj_grid g, const hjd::DevGrid& d, int scheme, int cl
     bool jit = hjk::jit_prepare(d, scheme, g->threads);
     if (!(g->gexec && g->g_per == k && g->g_dt == dt && g->g_scheme == scheme &&
           g->g_clamp == clamp && g->g_band == band && g->g_margin == margin &&
-          g->g_threads == g->threads && g->g_jit == jit)) {
+          g->g_threads == g->threads && g->g_tile_rows == g->tile_rows && g->g_jit == jit)) {
       drop_graph(g);
       g->g_jit = jit;
       cudaGraph_t graph = nullptr;
@@ -207,6 +211,7 @@ static hj_status run_window(hj_grid g, const hjd::DevGrid& d, int scheme, int cl
       g->g_band = band;
       g->g_margin = margin;
       g->g_threads = g->threads;
+      g->g_tile_rows = g->tile_rows;
     }
     HJ_CU(cudaGraphLaunch(g->gexec, g->stream));
     hjk::g_launches.fetch_add(3ull * (unsigned long long)k);
@@ -217,11 +222,39 @@ static hj_status run_window(hj_grid g, const hjd::DevGrid& d, int scheme, int cl
   return HJ_OK;
 }
 
-// Block sizes tried by the autotuner, and the process-wide choices per
-// (model, ndim, scheme, grid shape).
-static const int kCandidates[3] = {128, 256, 512};
+// Launch shapes tried by the autotuner: the flat mapping at three block
+// sizes, and row tiles of the few line counts that fill their warps best.
+// The process-wide choices per (model, ndim, scheme, grid shape).
+struct Shape {
+  int threads;    // flat mapping: threads per block
+  int tile_rows;  // > 0: row tiles of this many lines (threads follow from it)
+};
+static const int kFlatCandidates[3] = {128, 256, 512};
 static std::mutex g_tune_mu;
-static std::map<std::string, int> g_tuned;
+static std::map<std::string, Shape> g_tuned;
+
+// Row-tile line counts worth timing for lines of n nodes: tiles of 128 to
+// 1024 threads, ranked by the fraction of their lanes that hold a node.
+static std::vector<int> tile_candidates(const hj_grid g) {
+  int n = g->n[g->ndim - 1];
+  long long lines = g->npts / n;
+  std::vector<std::pair<double, int>> scored;
+  for (int r = 1; r * n <= hjk::kTileMaxThreads && r <= lines; ++r) {
+    int t = (r * n + 31) / 32 * 32;
+    if (t < 128) continue;
+    scored.push_back({-(double)(r * n) / t - 1e-6 * r, r});
+  }
+  std::sort(scored.begin(), scored.end());
+  std::vector<int> out;
+  for (size_t i = 0; i < scored.size() && out.size() < 3; ++i) out.push_back(scored[i].second);
+  return out;
+}
+
+static bool tile_fits(const hj_grid g, int rows) {
+  hjd::DevGrid d = devgrid(g);
+  const void* f[3] = {g->W, g->A, g->B};
+  return hjk::tile_ok(d, rows, f, 3);
+}
 
 static std::string tune_key(const hj_grid g, int scheme) {
   std::string k = std::to_string(g->model) + "/" + std::to_string(scheme);
@@ -229,17 +262,21 @@ static std::string tune_key(const hj_grid g, int scheme) {
   return k;
 }
 
-// Pick the stage-kernel block size for this grid: time a few TVD-RK3 steps
-// of each candidate on the grid's own current field, keep the fastest.  W is
-// saved to the snapshot field first and restored afterwards, so the grid's
-// value is unchanged.  Choices are cached per grid shape for the process.
+// Pick the stage kernels' launch shape for this grid: time a few TVD-RK3
+// steps of each candidate (flat blocks of 128/256/512 threads, row tiles of
+// the best-filling line counts) on the grid's own current field, keep the
+// fastest.  Every candidate computes the same values.  W is saved to the
+// snapshot field first and restored afterwards, so the grid's value is
+// unchanged.  Choices are cached per grid shape for the process.
 hj_status autotune(hj_grid g, int scheme, int clamp) {
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tuned.find(tune_key(g, scheme));
     if (it != g_tuned.end()) {
-      g->threads = it->second;
+      g->threads = it->second.threads;
+      g->tile_rows = tile_fits(g, it->second.tile_rows) ? it->second.tile_rows : 0;
       g->tuned_scheme = scheme;
+      drop_graph(g);
       return HJ_OK;
     }
   }
@@ -247,29 +284,61 @@ hj_status autotune(hj_grid g, int scheme, int clamp) {
   if (st != HJ_OK) return st;
   double dt = cfl_dt(g, 0.5);
   if (!(dt > 0.0)) dt = 1e-3;
-  hjd::DevGrid d = devgrid(g);
-  if (!g->has_value) HJ_CU(hjk::launch_init(d, g->W, g->snap, 0, g->stream));
+  if (!g->has_value) {
+    hjd::DevGrid d0 = devgrid(g);
+    HJ_CU(hjk::launch_init(d0, g->W, g->snap, 0, g->stream));
+  }
   size_t bytes = (size_t)g->npts * sizeof(float);
   HJ_CU(cudaMemcpyAsync(g->snap, g->W, bytes, cudaMemcpyDeviceToDevice, g->stream));
   long long steps = std::max(2ll, std::min(20ll, 400000000ll / std::max(1ll, g->npts)));
+  std::vector<Shape> cands;
+  for (int c : kFlatCandidates) cands.push_back({c, 0});
+  for (int r : tile_candidates(g))
+    if (tile_fits(g, r)) cands.push_back({256, r});
+  Shape saved{g->threads, g->tile_rows};
+  // grids that run shape-specialised kernels are timed with them: start the
+  // compiles of every candidate and wait for them (bounded), else time the
+  // precompiled kernels
+  bool use_jit = false;
+  if (hjk::jit_wanted(devgrid(g))) {
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+      bool all = true;
+      for (const Shape& c : cands) {
+        g->threads = c.threads;
+        g->tile_rows = c.tile_rows;
+        all = hjk::jit_prepare(devgrid(g), scheme, c.threads) && all;
+      }
+      if (all) {
+        use_jit = true;
+        break;
+      }
+      if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(120)) break;
+      std::this_thread::sleep_for(std::chrono::milliseconds(20));
+    }
+  }
   cudaEvent_t e0, e1;
   HJ_CU(cudaEventCreate(&e0));
   HJ_CU(cudaEventCreate(&e1));
-  int best = g->threads;
+  Shape best = saved;
   float best_ms = 1e30f;
-  int saved = g->threads;
-  for (int c : kCandidates) {
-    g->threads = c;
-    cudaError_t e = enqueue_steps(g, d, scheme, clamp, 0.f, 0, (float)dt, 1, false, g->stream);
+  for (const Shape& c : cands) {
+    g->threads = c.threads;
+    g->tile_rows = c.tile_rows;
+    hjd::DevGrid d = devgrid(g);
+    // one untimed step per candidate, then the timed ones
+    cudaError_t e = enqueue_steps(g, d, scheme, clamp, 0.f, 0, (float)dt, 1, false, g->stream,
+                                  use_jit);
     if (e == cudaSuccess) e = cudaEventRecord(e0, g->stream);
     if (e == cudaSuccess)
-      e = enqueue_steps(g, d, scheme, clamp, 0.f, 0, (float)dt, steps, false, g->stream);
+      e = enqueue_steps(g, d, scheme, clamp, 0.f, 0, (float)dt, steps, false, g->stream, use_jit);
     if (e == cudaSuccess) e = cudaEventRecord(e1, g->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0.f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
     if (e != cudaSuccess) {
-      g->threads = saved;
+      g->threads = saved.threads;
+      g->tile_rows = saved.tile_rows;
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
       return fail(HJ_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
@@ -283,7 +352,8 @@ hj_status autotune(hj_grid g, int scheme, int clamp) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   HJ_CU(cudaStreamSynchronize(g->stream));
-  g->threads = best;
+  g->threads = best.threads;
+  g->tile_rows = best.tile_rows;
   g->tuned_scheme = scheme;
   drop_graph(g);
   std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -295,6 +365,112 @@ static float bits_to_float(unsigned b) {
   float f;
   std::memcpy(&f, &b, 4);
   return f;
+}
+
+// Localized stepping (hj_solve_opts.local_tol > 0).  Window by window:
+//   - the first window steps every slab;
+//   - after each window a mask kernel turns the per-slab changes into the
+//     slabs that step (changed by more than local_tol, or within
+//     local_margin slabs of one that did) and the rings on which stages 1
+//     and 2 are recomputed (2 and 1 stencil radii further), and a list
+//     kernel turns them into the row tiles of each stage;
+//   - the next window launches exactly those tiles; stage 3 commits only
+//     stepping slabs, the others keep W and their snapshot.
+// The stop test is the usual one over the nodes that step.  One read-back
+// per window carries the residual and the three list lengths.
+hj_status solve_local(hj_grid g, const hj_solve_opts& o, double dt, hj_solve_stats& stats,
+                      std::chrono::steady_clock::time_point t0) {
+  if (g->tile_rows <= 0) {
+    for (int r : tile_candidates(g))
+      if (tile_fits(g, r)) {
+        g->tile_rows = r;
+        break;
+      }
+    if (g->tile_rows <= 0)
+      return fail(HJ_ERR_ARG, "localized stepping needs row tiles, and none fits this grid");
+    drop_graph(g);
+  }
+  hjd::DevGrid d = devgrid(g);
+  hjk::LocalLayout L = hjk::local_layout(d);
+  if (g->local_slabs != L.nslabs || g->local_tiles != L.ntiles) {
+    cudaFree(g->slab_resid);
+    cudaFree(g->slab_masks);
+    cudaFree(g->tile_lists);
+    g->slab_resid = nullptr;
+    g->slab_masks = nullptr;
+    g->tile_lists = nullptr;
+    g->local_slabs = g->local_tiles = 0;
+    HJ_CU(cudaMalloc(&g->slab_resid, (size_t)L.nslabs * sizeof(unsigned)));
+    HJ_CU(cudaMalloc(&g->slab_masks, 3 * (size_t)L.nslabs));
+    HJ_CU(cudaMalloc(&g->tile_lists, 3 * (size_t)L.ntiles * sizeof(int)));
+    g->local_slabs = L.nslabs;
+    g->local_tiles = L.ntiles;
+  }
+  if (!g->tile_counts) HJ_CU(cudaMalloc(&g->tile_counts, 4 * sizeof(int)));
+  if (!g->tile_counts_h) HJ_CU(cudaMallocHost(&g->tile_counts_h, 4 * sizeof(int)));
+  cudaStream_t s = g->stream;
+  const float fdt = (float)dt;
+  long long per = (long long)std::ceil(o.check_dt / dt - 1e-9);
+  if (per < 1) per = 1;
+  int counts[3] = {L.ntiles, L.ntiles, L.ntiles};
+  bool first = true;
+  double tiles_run = 0.0, tiles_full = 0.0;
+  const int t = g->threads;
+  for (;;) {
+    long long todo = per;
+    if (o.max_steps > 0 && stats.steps + todo > o.max_steps) todo = o.max_steps - stats.steps;
+    HJ_CU(cudaMemsetAsync(g->dscal + 4, 0, sizeof(unsigned), s));
+    HJ_CU(cudaMemsetAsync(g->slab_resid, 0, (size_t)L.nslabs * sizeof(unsigned), s));
+    hjd::StageArgs a1{g->W, g->W, g->A, nullptr, nullptr, fdt, 0, o.clamp, (float)o.band,
+                      o.band_margin};
+    hjd::StageArgs a2{g->A, g->W, g->B, nullptr, nullptr, fdt, 0, o.clamp, (float)o.band,
+                      o.band_margin};
+    hjd::StageArgs a3{g->B, g->W, g->W, g->snap, g->dscal + 4, fdt, 0, o.clamp, (float)o.band,
+                      o.band_margin};
+    if (!first) {
+      a1.tiles = g->tile_lists;
+      a2.tiles = g->tile_lists + L.ntiles;
+      a3.tiles = g->tile_lists + 2 * L.ntiles;
+      a1.ntiles = counts[0];
+      a2.ntiles = counts[1];
+      a3.ntiles = counts[2];
+      a3.live = g->slab_masks;
+    }
+    a3.slab_resid = g->slab_resid;
+    for (long long i = 0; i < todo; ++i) {
+      HJ_CU(hjk::launch_stage(d, o.scheme, 1, a1, s, t));
+      HJ_CU(hjk::launch_stage(d, o.scheme, 2, a2, s, t));
+      a3.check = (i == todo - 1) ? 1 : 0;
+      HJ_CU(hjk::launch_stage(d, o.scheme, 3, a3, s, t));
+    }
+    tiles_run += (double)todo * (counts[0] + counts[1] + counts[2]);
+    tiles_full += (double)todo * 3.0 * L.ntiles;
+    HJ_CU(hjk::launch_local_lists(d, o.scheme, g->slab_resid, (float)o.local_tol, o.local_margin,
+                                  g->slab_masks, g->tile_lists, g->tile_counts, s));
+    HJ_CU(cudaMemcpyAsync(g->hscal + 4, g->dscal + 4, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    HJ_CU(cudaMemcpyAsync(g->tile_counts_h, g->tile_counts, 3 * sizeof(int),
+                          cudaMemcpyDeviceToHost, s));
+    HJ_CU(cudaStreamSynchronize(s));
+    for (int q = 0; q < 3; ++q) counts[q] = g->tile_counts_h[q];
+    first = false;
+    stats.steps += todo;
+    stats.windows += 1;
+    stats.stepped = tiles_full > 0.0 ? tiles_run / tiles_full : 1.0;
+    float r = bits_to_float(g->hscal[4]);
+    stats.residual = r;
+    if (!std::isfinite(r)) return fail(HJ_ERR_DIVERGED, "non-finite value after %lld steps", stats.steps);
+    if ((double)r < o.tol) {
+      stats.converged = 1;
+      return HJ_OK;
+    }
+    if (o.max_steps > 0 && stats.steps >= o.max_steps)
+      return fail(HJ_ERR_NOT_CONVERGED, "step cap %lld reached (residual %g)", o.max_steps,
+                  (double)r);
+    double ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (o.max_wall_ms > 0.0 && ms > o.max_wall_ms)
+      return fail(HJ_ERR_NOT_CONVERGED, "wall-time cap reached (residual %g)", (double)r);
+  }
 }
 
 }  // namespace hja
@@ -324,6 +500,8 @@ void hj_default_opts(hj_solve_opts* o) {
   o->band = 0.0;
   o->autotune = 0;
   o->band_margin = 0;
+  o->local_tol = 0.0;
+  o->local_margin = 2;
 }
 
 void hj_grid_destroy(hj_grid g) {
@@ -339,6 +517,11 @@ void hj_grid_destroy(hj_grid g) {
     cudaFree(g->dscal);
     cudaFree(g->qbuf);
     cudaFree(g->fdev);
+    cudaFree(g->slab_resid);
+    cudaFree(g->slab_masks);
+    cudaFree(g->tile_lists);
+    cudaFree(g->tile_counts);
+    if (g->tile_counts_h) cudaFreeHost(g->tile_counts_h);
     if (g->fhost) cudaFreeHost(g->fhost);
     if (g->hscal) cudaFreeHost(g->hscal);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
@@ -592,6 +775,29 @@ hj_status hj_autotune(hj_grid g, int scheme, int* threads_out) {
   return HJ_OK;
 }
 
+hj_status hj_set_launch_shape(hj_grid g, int threads, int tile_rows) {
+  if (!g) return fail(HJ_ERR_ARG, "grid is NULL");
+  if (threads != 128 && threads != 256 && threads != 512)
+    return fail(HJ_ERR_ARG, "threads must be 128, 256 or 512");
+  if (tile_rows < 0) return fail(HJ_ERR_ARG, "tile_rows must be >= 0");
+  if (tile_rows > 0 && !tile_fits(g, tile_rows))
+    return fail(HJ_ERR_ARG, "row tiles of %d lines of %d nodes do not fit (at most %d nodes and "
+                "%lld lines)", tile_rows, g->n[g->ndim - 1], hjk::kTileMaxThreads,
+                g->npts / g->n[g->ndim - 1]);
+  g->threads = threads;
+  g->tile_rows = tile_rows;
+  g->tuned_scheme = 0;
+  drop_graph(g);
+  return HJ_OK;
+}
+
+hj_status hj_get_launch_shape(hj_grid g, int* threads, int* tile_rows) {
+  if (!g) return fail(HJ_ERR_ARG, "grid is NULL");
+  if (threads) *threads = g->threads;
+  if (tile_rows) *tile_rows = g->tile_rows;
+  return HJ_OK;
+}
+
 hj_status hj_alpha(hj_grid g, double* alpha_out) {
   if (!g || !alpha_out) return fail(HJ_ERR_ARG, "NULL argument");
   if (g->model < 0) return fail(HJ_ERR_STATE, "dynamics not set");
@@ -611,7 +817,7 @@ hj_status hj_solve(hj_grid g, int mode, const hj_solve_opts* o_in, hj_solve_stat
   if (o_in) o = *o_in;
   if (mode != HJ_COLD && mode != HJ_WARM) return fail(HJ_ERR_ARG, "mode must be HJ_COLD or HJ_WARM");
   if (!(o.cfl > 0.0) || !(o.tol >= 0.0) || !(o.check_dt > 0.0) || o.dt < 0.0 || !(o.band >= 0.0) ||
-      o.band_margin < 0)
+      o.band_margin < 0 || !(o.local_tol >= 0.0) || o.local_margin < 0 || o.local_margin > 64)
     return fail(HJ_ERR_ARG, "bad solve options");
   if (o.clamp != HJ_CLAMP_VI && o.clamp != HJ_CLAMP_MONOTONE) return fail(HJ_ERR_ARG, "bad clamp");
   hj_status st = validate_ready(g, o.scheme);
@@ -621,6 +827,7 @@ hj_status hj_solve(hj_grid g, int mode, const hj_solve_opts* o_in, hj_solve_stat
   DeviceGuard dg(g->device);
   hj_solve_stats stats;
   std::memset(&stats, 0, sizeof(stats));
+  stats.stepped = 1.0;
 
   if ((st = ensure_alpha(g)) != HJ_OK) return st;
   if (o.autotune && g->tuned_scheme != o.scheme && (st = autotune(g, o.scheme, o.clamp)) != HJ_OK)
@@ -641,6 +848,9 @@ hj_status hj_solve(hj_grid g, int mode, const hj_solve_opts* o_in, hj_solve_stat
                         false, g->stream));
     HJ_CU(cudaStreamSynchronize(g->stream));
     stats.steps = o.fixed_steps;
+  } else if (o.local_tol > 0.0) {
+    rc = solve_local(g, o, dt, stats, t0);
+    if (rc != HJ_OK && rc != HJ_ERR_NOT_CONVERGED && rc != HJ_ERR_DIVERGED) return rc;
   } else {
     long long per = (long long)std::ceil(o.check_dt / dt - 1e-9);
     if (per < 1) per = 1;

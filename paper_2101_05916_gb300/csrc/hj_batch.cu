@@ -463,6 +463,7 @@ hj_status Runner::collect(int k, hj_solve_stats* out) {
   st.windows = c.windows;
   st.wall_ms = s.wall_ms;
   st.converged = c.status == S_CONVERGED;
+  st.stepped = 1.0;
   hj_status rc = HJ_OK;
   if (s.fixed) {
     st.converged = 0;

@@ -35,8 +35,11 @@ struct DevGrid {
   int npts;
   int plane;           // nodes of one thread slab: all axes but the first of a 4-D grid,
                        // every node of a grid with ndim <= 3
-  unsigned div_m[2];   // n[ndim-1], n[ndim-2] as multiply-shift reciprocals
-  int div_s[2];
+  unsigned div_m[3];   // n[ndim-1], n[ndim-2], n[ndim-3] as multiply-shift reciprocals
+  int div_s[3];
+  int nrows;           // lines along the fastest axis: npts / n[ndim-1]
+  int tile_rows;       // > 0: row-tile kernels, this many fastest-axis lines per block;
+                       // 0: one node per thread over flattened slabs
   float lo[MAXD];
   float h[MAXD];
   double lo_d[MAXD];   // the same box in double, for interpolation
@@ -72,7 +75,24 @@ struct StageArgs {
   int clamp;           // 0: min(W3, l); 1: min(W3, l, W)
   float band;          // > 0: residual only where min(|W|, |snap|) <= band
   int margin;          // residual only at nodes >= margin cells from every face
+  // Localized stepping (row-tile kernels only; all null in a plain solve):
+  const int* tiles;          // block b runs row tile tiles[b] (null: tile b)
+  int ntiles;                // entries of tiles (host side: the launch's block count)
+  const unsigned char* live; // stage 3: nonzero where the node's slab steps (null: all)
+  unsigned* slab_resid;      // stage 3 with check: per-slab max |W - snap| over every
+                             // node, as float bits (null: not kept)
 };
+
+// Slabs of a grid, the units of localized stepping: the lines of the two
+// slowest axes of a 4-D grid (index i0 n1 + i1), the first axis of a 2-D or
+// 3-D grid, the whole of a 1-D grid.  A slab spans every node of the axes it
+// leaves free.
+template <int D>
+__device__ __forceinline__ int slab_of(const DevGrid& g, const int (&idx)[D]) {
+  if constexpr (D == 4) return idx[0] * g.n[1] + idx[1];
+  else if constexpr (D >= 2) return idx[0];
+  else return 0;
+}
 
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;
@@ -435,22 +455,32 @@ struct Slopes<5> {
 };
 
 // L(src) at node p with multi-index idx; also returns src[p] in `center`.
-// The last axis is the fastest (stride 1); its line is loaded branch-free at
-// immediate offsets (load_fast_line).  src needs at least 3 readable guard
-// floats before its first and after its last node.
+// The last axis is the fastest (stride 1).  Its line comes either from
+// `fast`, a shared-memory copy of the node's row with its ghost values
+// already in place (fast[k] is the line value at offset k, k = -R..R), or,
+// when fast is null, from global memory branch-free at immediate offsets
+// (load_fast_line); src then needs at least 3 readable guard floats before
+// its first and after its last node.  Both give the same values.
 template <int D, int S, int M>
 __device__ __forceinline__ float lf_rhs(const DevGrid& g, const float* __restrict__ src, int p,
-                                        const int (&idx)[D], const float (&x)[D], float& center) {
+                                        const int (&idx)[D], const float (&x)[D], float& center,
+                                        const float* fast = nullptr) {
   constexpr int R = Slopes<S>::R;
   float pbar[D];
   float diss = 0.f;
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     float v[2 * R + 1];
-    if (d == D - 1)
-      load_fast_line<R>(src, p, idx[d], g.n[d], v);
-    else
+    if (d == D - 1) {
+      if (fast) {
+#pragma unroll
+        for (int k = -R; k <= R; ++k) v[k + R] = fast[k];
+      } else {
+        load_fast_line<R>(src, p, idx[d], g.n[d], v);
+      }
+    } else {
       load_line<R>(src, p, g.stride[d], idx[d], g.n[d], v);
+    }
     if (d == D - 1) center = v[R];
     float pm, pp;
     Slopes<S>::eval(v, g, d, pm, pp);

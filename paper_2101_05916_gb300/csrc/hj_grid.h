@@ -42,9 +42,19 @@ struct hj_grid_s {
   double* fhost = nullptr;    // ... and its pinned host mirror
   size_t fcap = 0;            // doubles in each
 
+  // localized stepping (allocated on first use): per-slab window change,
+  // slab masks, the three stages' tile lists and their lengths
+  unsigned* slab_resid = nullptr;
+  unsigned char* slab_masks = nullptr;
+  int* tile_lists = nullptr;
+  int* tile_counts = nullptr;     // device, 3 ints
+  int* tile_counts_h = nullptr;   // pinned host mirror
+  long long local_slabs = 0, local_tiles = 0;  // sizes the buffers were made for
+
   bool has_value = false;
   bool alpha_valid = false;
-  int threads = 256;        // stage-kernel block size (hj_autotune may change it)
+  int threads = 256;        // stage-kernel block size of the flat mapping (hj_autotune may change it)
+  int tile_rows = 0;        // > 0: row-tile stage kernels with this many lines per block
   int tuned_scheme = 0;     // scheme the block size was tuned for (0 = not tuned)
   float alpha[HJ_MAX_DIM] = {0, 0, 0, 0};
 
@@ -55,6 +65,7 @@ struct hj_grid_s {
   float g_band = 0.f;
   int g_margin = 0;
   int g_threads = 0;
+  int g_tile_rows = 0;
   bool g_jit = false;  // the cached graph holds shape-specialised kernels
 };
 

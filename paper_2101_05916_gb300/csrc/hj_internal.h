@@ -15,6 +15,34 @@ extern std::atomic<unsigned long long> g_launches;
 // Threads per block of the stencil kernels.
 constexpr int kStageThreads = 256;
 
+// Launch shape of the row-tile stage kernels (DevGrid::tile_rows > 0):
+// blocks of ceil(tile_rows * n_last / 32) warps, one block per tile_rows
+// lines of the fastest axis, and the shared-memory bytes of one tile.
+struct TileShape {
+  int threads = 0;
+  unsigned blocks = 0;
+  size_t smem = 0;
+};
+constexpr int kTileMaxThreads = 1024;
+TileShape tile_shape(const hjd::DevGrid& g, int scheme);
+// Whether row tiles of tile_rows lines fit this grid (at most kTileMaxThreads
+// nodes per tile, no more lines than the grid has) and every field is
+// 16-byte aligned (the staging loads are 16 bytes wide).
+bool tile_ok(const hjd::DevGrid& g, int tile_rows, const void* const* fields, int nfields);
+
+// Localized stepping over slabs (hjd::slab_of): the slab lattice is
+// s0 x s1, and every slab holds rows_per_slab consecutive fastest-axis lines.
+struct LocalLayout {
+  int s0 = 1, s1 = 1, nslabs = 1, rows_per_slab = 1, ntiles = 0;
+};
+LocalLayout local_layout(const hjd::DevGrid& g);
+// From the window's per-slab changes (float bits, nslabs entries): the slab
+// masks (3 x nslabs bytes: live, ring2, ring1) and the row-tile lists of the
+// three stages (3 x ntiles ints) with their lengths in counts[0..2].
+cudaError_t launch_local_lists(const hjd::DevGrid& g, int scheme, const unsigned* slab_resid,
+                               float thr, int margin, unsigned char* masks, int* lists,
+                               int* counts, cudaStream_t s);
+
 // Streaming multiprocessors of the current device (read once per device).
 int num_sms();
 // Blocks of a grid-stride launch over `work` items: enough to cover them,

@@ -78,7 +78,7 @@ const Nvrtc& nvrtc() {
 // model constants that stay fixed while a grid is updated (the disturbance
 // bound, alpha and the constraint box stay run-time values).
 struct Key {
-  int device, ndim, model, scheme, threads, con_kind;
+  int device, ndim, model, scheme, threads, tile_rows, con_kind;
   unsigned con_mask;
   int n[hjd::MAXD];
   unsigned geom[5 * hjd::MAXD];  // float bits of lo, h, ih, hih, wfloor
@@ -134,6 +134,7 @@ Key key_of(const hjd::DevGrid& g, int scheme, int threads) {
   k.model = g.model;
   k.scheme = scheme;
   k.threads = threads;
+  k.tile_rows = g.tile_rows;
   k.con_kind = g.con_kind;
   k.con_mask = g.con_mask;
   for (int d = 0; d < g.ndim; ++d) {
@@ -170,10 +171,30 @@ std::string source(const hjd::DevGrid& g, int scheme, int threads) {
                 g.con_mask);
   s += buf;
   std::snprintf(buf, sizeof(buf),
-                "  c.npts = %d; c.plane = %d;\n  c.div_m[0] = %uu; c.div_s[0] = %d;\n"
-                "  c.div_m[1] = %uu; c.div_s[1] = %d;\n  return c;\n}\n",
-                g.npts, g.plane, g.div_m[0], g.div_s[0], g.div_m[1], g.div_s[1]);
+                "  c.npts = %d; c.plane = %d; c.nrows = %d; c.tile_rows = %d;\n"
+                "  c.div_m[0] = %uu; c.div_s[0] = %d;\n"
+                "  c.div_m[1] = %uu; c.div_s[1] = %d;\n  c.div_m[2] = %uu; c.div_s[2] = %d;\n"
+                "  return c;\n}\n",
+                g.npts, g.plane, g.nrows, g.tile_rows, g.div_m[0], g.div_s[0], g.div_m[1],
+                g.div_s[1], g.div_m[2], g.div_s[2]);
   s += buf;
+  if (g.tile_rows > 0) {
+    // row tiles: the tile's shared memory is a static array of its exact size
+    TileShape ts = tile_shape(g, scheme);
+    int pitch = g.n[g.ndim - 1] + 2 * (scheme == 5 ? 3 : (scheme == 2 ? 2 : 1));
+    for (int st = 1; st <= 3; ++st) {
+      std::snprintf(buf, sizeof(buf),
+                    "extern \"C\" __global__ void __launch_bounds__(%d)\n"
+                    "hj_stage_%d(const hjd::DevGrid g, const hjd::StageArgs a) {\n"
+                    "  __shared__ float sm[%d];\n",
+                    ts.threads, st, g.tile_rows * pitch);
+      s += buf;
+      std::snprintf(buf, sizeof(buf), "  hjd::tile_body<%d, %d, %d, %d>(hj_fixed(g), a, sm);\n}\n",
+                    g.ndim, scheme, g.model, st);
+      s += buf;
+    }
+    return s;
+  }
   for (int st = 1; st <= 3; ++st) {
     std::snprintf(buf, sizeof(buf),
                   "extern \"C\" __global__ void __launch_bounds__(%d)\n"
@@ -337,11 +358,18 @@ cudaError_t jit_launch(const hjd::DevGrid& g, int scheme, int stage, const hjd::
   if (!jit_wanted(g)) return cudaSuccess;
   Entry* e = lookup(g, scheme, threads, !capturing(s));
   if (!e) return cudaSuccess;
-  unsigned bx = (unsigned)((g.plane + threads - 1) / threads);
-  unsigned by = g.ndim == 4 ? (unsigned)g.n[0] : 1u;
+  dim3 grid, block;
+  if (g.tile_rows > 0) {
+    TileShape ts = tile_shape(g, scheme);
+    grid = dim3(a.tiles ? (unsigned)a.ntiles : ts.blocks, 1, 1);
+    block = dim3(ts.threads, 1, 1);
+  } else {
+    grid = dim3((unsigned)((g.plane + threads - 1) / threads), g.ndim == 4 ? (unsigned)g.n[0] : 1u,
+                1);
+    block = dim3(threads, 1, 1);
+  }
   void* args[] = {(void*)&g, (void*)&a};
-  cudaError_t err = cudaLaunchKernel((const void*)e->stage[stage - 1], dim3(bx, by, 1),
-                                     dim3(threads, 1, 1), args, 0, s);
+  cudaError_t err = cudaLaunchKernel((const void*)e->stage[stage - 1], grid, block, args, 0, s);
   if (err == cudaSuccess) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
     *used = true;
@@ -357,7 +385,21 @@ void jit_enable(int on) { g_enabled.store(on ? 1 : 0); }
 
 }  // namespace hjk
 
+static hj_status jit_check(int ndim, const int* n, int model, int scheme, int threads,
+                           int tile_rows);
+
 extern "C" hj_status hj_jit_check(int ndim, const int* n, int model, int scheme, int threads) {
+  return jit_check(ndim, n, model, scheme, threads, 0);
+}
+
+extern "C" hj_status hj_jit_check_tiles(int ndim, const int* n, int model, int scheme,
+                                        int tile_rows) {
+  if (tile_rows <= 0) return hja::fail(HJ_ERR_ARG, "tile_rows must be > 0");
+  return jit_check(ndim, n, model, scheme, 256, tile_rows);
+}
+
+static hj_status jit_check(int ndim, const int* n, int model, int scheme, int threads,
+                           int tile_rows) {
   if (ndim < 1 || ndim > HJ_MAX_DIM || !n) return hja::fail(HJ_ERR_ARG, "bad grid shape");
   if (model != HJ_DRIFT && model != HJ_QUAD_Z && model != HJ_QUAD_X4)
     return hja::fail(HJ_ERR_ARG, "unknown model %d", model);
@@ -384,7 +426,11 @@ extern "C" hj_status hj_jit_check(int ndim, const int* n, int model, int scheme,
   g.npts = npts;
   g.model = model;
   g.con_kind = hjd::C_BOX;
+  g.tile_rows = tile_rows;
   hjd::DevGrid d = hja::devgrid(&g);
+  if (tile_rows > 0 && ((long long)tile_rows * n[ndim - 1] > hjk::kTileMaxThreads ||
+                        tile_rows > d.nrows))
+    return hja::fail(HJ_ERR_ARG, "row tile does not fit the grid");
   if (!hjk::nvrtc().ok) return hja::fail(HJ_ERR_CUDA, "NVRTC could not be loaded");
   std::string log;
   std::vector<char> cubin = hjk::compile(hjk::source(d, scheme, threads), &log);

@@ -18,6 +18,7 @@
 // cover adjacent rows, so the +-3 neighbours along the two fast axes are L1
 // hits.
 #include <algorithm>
+#include <cstdint>
 #include <cstdio>
 
 #include "hj_internal.h"
@@ -37,6 +38,14 @@ __global__ void __launch_bounds__(THREADS) stage_kernel(const DevGrid g, const S
   if constexpr (STAGE == 3) {
     if (a.check) hjd::block_max_bits(r, a.resid);
   }
+}
+
+// Row-tile variant: block b stages lines [b R, b R + R) of the fastest axis
+// in shared memory (hjd::stage_tile) and computes their nodes.
+template <int D, int S, int M, int STAGE, int MAXT>
+__global__ void __launch_bounds__(MAXT) tile_kernel(const DevGrid g, const StageArgs a) {
+  extern __shared__ float sm[];
+  hjd::tile_body<D, S, M, STAGE>(g, a, sm);
 }
 
 template <int D>
@@ -191,9 +200,29 @@ static void stage_launch(const DevGrid& g, int stage, const StageArgs& a, cudaSt
   }
 }
 
+template <int D, int S, int M, int MAXT>
+static void tile_launch(const DevGrid& g, int stage, const StageArgs& a, const TileShape& ts,
+                        cudaStream_t s) {
+  dim3 grid(a.tiles ? (unsigned)a.ntiles : ts.blocks), block(ts.threads);
+  if (grid.x == 0) return;
+  switch (stage) {
+    case 1: tile_kernel<D, S, M, 1, MAXT><<<grid, block, ts.smem, s>>>(g, a); break;
+    case 2: tile_kernel<D, S, M, 2, MAXT><<<grid, block, ts.smem, s>>>(g, a); break;
+    default: tile_kernel<D, S, M, 3, MAXT><<<grid, block, ts.smem, s>>>(g, a); break;
+  }
+}
+
 template <int D, int S, int M>
 static cudaError_t stage_dispatch(const DevGrid& g, int stage, const StageArgs& a, int threads,
                                   cudaStream_t s) {
+  if (g.tile_rows > 0) {
+    TileShape ts = tile_shape(g, S);
+    if (ts.threads <= 256) tile_launch<D, S, M, 256>(g, stage, a, ts, s);
+    else if (ts.threads <= 512) tile_launch<D, S, M, 512>(g, stage, a, ts, s);
+    else tile_launch<D, S, M, 1024>(g, stage, a, ts, s);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+  }
   switch (threads) {
     case 128: stage_launch<D, S, M, 128>(g, stage, a, s); break;
     case 512: stage_launch<D, S, M, 512>(g, stage, a, s); break;
@@ -222,9 +251,32 @@ bool stage_supported(int model, int ndim, int scheme) {
   return false;
 }
 
+TileShape tile_shape(const DevGrid& g, int scheme) {
+  TileShape t;
+  int radius = scheme == 5 ? 3 : (scheme == 2 ? 2 : 1);
+  int n = g.n[g.ndim - 1];
+  int rows = g.tile_rows < g.nrows ? g.tile_rows : g.nrows;
+  t.threads = (rows * n + 31) / 32 * 32;
+  t.blocks = (unsigned)((g.nrows + g.tile_rows - 1) / g.tile_rows);
+  t.smem = (size_t)g.tile_rows * (size_t)(n + 2 * radius) * sizeof(float);
+  return t;
+}
+
+bool tile_ok(const DevGrid& g, int tile_rows, const void* const* fields, int nfields) {
+  if (tile_rows <= 0) return false;
+  long long nodes = (long long)tile_rows * g.n[g.ndim - 1];
+  if (nodes > kTileMaxThreads || (long long)tile_rows > (long long)g.nrows) return false;
+  for (int i = 0; i < nfields; ++i)
+    if (reinterpret_cast<uintptr_t>(fields[i]) & 15u) return false;
+  return true;
+}
+
 cudaError_t launch_stage(const DevGrid& g, int scheme, int stage, const StageArgs& a, cudaStream_t s,
                          int threads, bool allow_jit) {
   if (threads != 128 && threads != 512) threads = 256;
+  if (g.tile_rows > 0 && (reinterpret_cast<uintptr_t>(a.src) & 15u)) return cudaErrorInvalidValue;
+  if (g.tile_rows <= 0 && (a.tiles || a.live || a.slab_resid)) return cudaErrorInvalidValue;
+  if (a.tiles && a.ntiles == 0) return cudaSuccess;
   if (allow_jit) {
     bool used = false;
     cudaError_t e = jit_launch(g, scheme, stage, a, s, threads, &used);
@@ -313,6 +365,97 @@ cudaError_t launch_prolong(const DevGrid& c, const float* Wc, const DevGrid& f, 
     default: return cudaErrorInvalidValue;
   }
   g_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------- localized stepping
+
+// Slab masks from the last window's per-slab changes.  A slab is raw-active
+// when its change exceeds thr.  With d the Chebyshev distance (in slabs,
+// over the s0 x s1 slab lattice) to the nearest raw-active slab:
+//   live  (d <= k):      steps and commits its nodes;
+//   ring2 (d <= k + R):  stage 2 is computed there, so that stage 3 at live
+//                        nodes reads valid W2 within its stencil radius R;
+//   ring1 (d <= k + 2R): stage 1 is computed there, so that stage 2 on ring2
+//                        reads valid W1.
+// k is the reactivation margin: a frozen slab wakes up when a slab within k
+// of it changed by more than thr in the last window.
+__global__ void local_masks_kernel(const unsigned* __restrict__ resid, int s0, int s1, float thr,
+                                   int k, int radius, unsigned char* live, unsigned char* ring2,
+                                   unsigned char* ring1) {
+  int sl = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sl >= s0 * s1) return;
+  int i = sl / s1, j = sl - i * s1;
+  int reach = k + 2 * radius;
+  int best = reach + 1;
+  int i_lo = max(0, i - reach), i_hi = min(s0 - 1, i + reach);
+  int j_lo = max(0, j - reach), j_hi = min(s1 - 1, j + reach);
+  for (int a = i_lo; a <= i_hi; ++a)
+    for (int b = j_lo; b <= j_hi; ++b)
+      if (__uint_as_float(resid[a * s1 + b]) > thr) best = min(best, max(abs(a - i), abs(b - j)));
+  live[sl] = best <= k;
+  ring2[sl] = best <= k + radius;
+  ring1[sl] = best <= k + 2 * radius;
+}
+
+// Tile lists of the next window: list q (q = 0, 1, 2 for stages 1, 2, 3)
+// gets every row tile that holds a line of a slab in mask q (ring1, ring2,
+// live).  counts[q] must be zero on entry.  The order within a list does not
+// matter: tiles are independent within a stage.
+__global__ void local_lists_kernel(int ntiles, int tile_rows, int nrows, int rows_per_slab,
+                                   const unsigned char* __restrict__ ring1,
+                                   const unsigned char* __restrict__ ring2,
+                                   const unsigned char* __restrict__ live, int* lists,
+                                   int* counts) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntiles) return;
+  int r0 = t * tile_rows, r1 = min(r0 + tile_rows, nrows) - 1;
+  int f = r0 / rows_per_slab, l = r1 / rows_per_slab;
+  bool m1 = false, m2 = false, m3 = false;
+  for (int sl = f; sl <= l; ++sl) {
+    m1 = m1 || ring1[sl];
+    m2 = m2 || ring2[sl];
+    m3 = m3 || live[sl];
+  }
+  if (m1) lists[atomicAdd(counts + 0, 1)] = t;
+  if (m2) lists[ntiles + atomicAdd(counts + 1, 1)] = t;
+  if (m3) lists[2 * ntiles + atomicAdd(counts + 2, 1)] = t;
+}
+
+LocalLayout local_layout(const DevGrid& g) {
+  LocalLayout L;
+  if (g.ndim == 4) {
+    L.s0 = g.n[0];
+    L.s1 = g.n[1];
+    L.rows_per_slab = g.n[2];
+  } else if (g.ndim >= 2) {
+    L.s0 = g.n[0];
+    L.s1 = 1;
+    L.rows_per_slab = g.ndim == 3 ? g.n[1] : 1;
+  } else {
+    L.s0 = 1;
+    L.s1 = 1;
+    L.rows_per_slab = 1;
+  }
+  L.nslabs = L.s0 * L.s1;
+  L.ntiles = g.tile_rows > 0 ? (g.nrows + g.tile_rows - 1) / g.tile_rows : 0;
+  return L;
+}
+
+cudaError_t launch_local_lists(const DevGrid& g, int scheme, const unsigned* slab_resid,
+                               float thr, int margin, unsigned char* masks, int* lists,
+                               int* counts, cudaStream_t s) {
+  LocalLayout L = local_layout(g);
+  int radius = scheme == 5 ? 3 : (scheme == 2 ? 2 : 1);
+  unsigned char *live = masks, *ring2 = masks + L.nslabs, *ring1 = masks + 2 * L.nslabs;
+  cudaError_t e = cudaMemsetAsync(counts, 0, 3 * sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  local_masks_kernel<<<(L.nslabs + 255) / 256, 256, 0, s>>>(slab_resid, L.s0, L.s1, thr, margin,
+                                                           radius, live, ring2, ring1);
+  local_lists_kernel<<<(L.ntiles + 255) / 256, 256, 0, s>>>(L.ntiles, g.tile_rows, g.nrows,
+                                                           L.rows_per_slab, ring1, ring2, live,
+                                                           lists, counts);
+  g_launches.fetch_add(2, std::memory_order_relaxed);
   return cudaGetLastError();
 }
 

@@ -47,14 +47,15 @@ class hj_solve_opts(ctypes.Structure):
                 ("max_steps", ctypes.c_longlong), ("fixed_steps", ctypes.c_longlong),
                 ("max_wall_ms", ctypes.c_double), ("clamp", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("band", ctypes.c_double),
-                ("autotune", ctypes.c_int), ("band_margin", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("band_margin", ctypes.c_int),
+                ("local_tol", ctypes.c_double), ("local_margin", ctypes.c_int)]
 
 
 class hj_solve_stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_longlong), ("t", ctypes.c_double),
                 ("residual", ctypes.c_double), ("dt", ctypes.c_double),
                 ("wall_ms", ctypes.c_double), ("converged", ctypes.c_int),
-                ("windows", ctypes.c_longlong)]
+                ("windows", ctypes.c_longlong), ("stepped", ctypes.c_double)]
 
     def as_dict(self) -> Dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -104,6 +105,9 @@ SIGNATURES = {
     "hj_jit_kernels": (_ll, []),
     "hj_jit_pending": (_ll, []),
     "hj_jit_check": (_i, [_i, _P(_i), _i, _i, _i]),
+    "hj_jit_check_tiles": (_i, [_i, _P(_i), _i, _i, _i]),
+    "hj_set_launch_shape": (_i, [_vp, _i, _i]),
+    "hj_get_launch_shape": (_i, [_vp, _P(_i), _P(_i)]),
     "hj_set_value": (_i, [_vp, _vp, _i]),
     "hj_get_value": (_i, [_vp, _vp, _i]),
     "hj_query_value": (_i, [_vp, _i, _P(_d), _P(_d)]),
@@ -261,9 +265,11 @@ def make_opts(scheme: int = HJ_WENO5, cfl: float = 0.5, dt: float = 0.0, tol: fl
               check_dt: float = 0.1, max_steps: int = 1000000, fixed_steps: int = 0,
               max_wall_ms: float = 0.0, clamp: int = HJ_CLAMP_VI,
               use_graph: bool = True, band: float = 0.0,
-              autotune: bool = False, band_margin: int = 0) -> hj_solve_opts:
+              autotune: bool = False, band_margin: int = 0, local_tol: float = 0.0,
+              local_margin: int = 2) -> hj_solve_opts:
     return hj_solve_opts(scheme, cfl, dt, tol, check_dt, max_steps, fixed_steps, max_wall_ms,
-                         clamp, 1 if use_graph else 0, band, 1 if autotune else 0, band_margin)
+                         clamp, 1 if use_graph else 0, band, 1 if autotune else 0, band_margin,
+                         local_tol, local_margin)
 
 
 def hj_solve(g: int, mode: int = HJ_COLD, opts: Optional[hj_solve_opts] = None,
@@ -412,6 +418,24 @@ def hj_jit_check(n: Sequence[int], model, scheme: int, threads: int = 256) -> No
     m = MODELS[model] if isinstance(model, str) else int(model)
     arr = (_i * len(n))(*[int(v) for v in n])
     _check(lib().hj_jit_check(len(n), arr, m, int(scheme), int(threads)))
+
+
+def hj_jit_check_tiles(n: Sequence[int], model, scheme: int, tile_rows: int) -> None:
+    """The same for the row-tile stage kernels of tile_rows lines per block."""
+    m = MODELS[model] if isinstance(model, str) else int(model)
+    arr = (_i * len(n))(*[int(v) for v in n])
+    _check(lib().hj_jit_check_tiles(len(n), arr, m, int(scheme), int(tile_rows)))
+
+
+def hj_set_launch_shape(g: int, threads: int = 256, tile_rows: int = 0) -> None:
+    _check(lib().hj_set_launch_shape(g, int(threads), int(tile_rows)))
+
+
+def hj_get_launch_shape(g: int):
+    """(threads per block of the flat mapping, tile_rows) of the grid."""
+    t, r = ctypes.c_int(), ctypes.c_int()
+    _check(lib().hj_get_launch_shape(g, ctypes.byref(t), ctypes.byref(r)))
+    return t.value, r.value
 
 
 def hj_jit_wait(timeout_s: float = 120.0) -> bool:
@@ -656,6 +680,12 @@ class Grid:
 
     def alpha(self) -> np.ndarray:
         return hj_alpha(self.handle, self.ndim)
+
+    def set_launch_shape(self, threads: int = 256, tile_rows: int = 0) -> None:
+        hj_set_launch_shape(self.handle, threads, tile_rows)
+
+    def launch_shape(self):
+        return hj_get_launch_shape(self.handle)
 
     def close(self) -> None:
         if getattr(self, "handle", None):

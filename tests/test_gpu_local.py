@@ -1,0 +1,119 @@
+"""Localized warm starting (Sec. VI, Discussion: update only where the value
+function still changes), built as localized stepping over slabs.
+
+After a local rise of the wind bound, the warm solve from the previous
+fixed point steps only the slabs that changed by more than local_tol in the
+last window (plus a reactivation margin), recomputing the first two RK
+stages on rings around them.  The statement checked here: the localized
+result equals the full warm solve's, and the FP64 oracle's warm solve, within
+the parity bar (1e-4 max|W|, sign agreement >= 99.99 % away from the zero
+level set), while stepping only part of the grid.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2101_05916_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-4
+SIGN_FRAC = 0.9999
+
+
+@pytest.fixture(scope="module")
+def hj():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2101_05916_gb300 import build, hj as hjmod
+    build.build()
+    hjmod.lib()
+    return hjmod
+
+
+def sign_agreement_far(a, b):
+    from paper_2101_05916_gb300 import scenarios
+    return scenarios.accuracy(a, b)["sign_agreement_far"]
+
+
+def local_case(hj, spec, scheme, base_field, raised_field, local_tol, dts=(0.0, 0.0), **kw):
+    g = hj.Grid.from_spec(spec)
+    g.set_disturbance_field(*base_field)
+    st0 = g.solve(hj.HJ_COLD, scheme=scheme, max_steps=50000, dt=dts[0], **kw)
+    assert st0["converged"]
+    prior = g.value()
+    g.set_disturbance_field(*raised_field)
+    full = g.solve(hj.HJ_WARM, scheme=scheme, max_steps=50000, dt=dts[1], **kw)
+    Wfull = g.value()
+    g.set_value(prior)
+    loc = g.solve(hj.HJ_WARM, scheme=scheme, max_steps=50000, local_tol=local_tol, dt=dts[1],
+                  **kw)
+    Wloc = g.value()
+    g.close()
+    assert full["converged"] and loc["converged"]
+    return st0, Wfull, full, Wloc, loc
+
+
+@pytest.mark.parametrize("scheme", [2, 5])
+def test_localized_update_z_matches_full_and_oracle(hj, scheme):
+    spec = wl.quad_z(121, 0.3)
+    base = wl.wind_field(spec, 0.3, 0.0, 0, 1.5, 0.4)
+    raised = wl.wind_field(spec, 0.3, 1.0, 0, 2.3, 0.15)
+    kw = dict(tol=1e-5)
+    st0, Wf, full, Wl, loc = local_case(hj, spec, scheme, base, raised, 1e-6, **kw)
+    scale = np.abs(Wf).max()
+    assert np.abs(Wl - Wf).max() <= REL * scale
+    assert sign_agreement_far(Wl, Wf) >= SIGN_FRAC
+    assert loc["stepped"] < 0.9, loc
+    # against the oracle's own warm solve from its own prior
+    Wp, _ = oracle.solve(spec, scheme=scheme, tol=1e-7, dfield=base, max_steps=80000)
+    Wo, sto = oracle.solve(spec, scheme=scheme, tol=1e-7, dfield=raised, warm=Wp,
+                           max_steps=80000)
+    assert sto["converged"]
+    assert np.abs(Wl - Wo).max() <= REL * np.abs(Wo).max()
+    assert sign_agreement_far(Wl, Wo) >= SIGN_FRAC
+
+
+def test_localized_update_x4_matches_full_warm_and_steps_less(hj):
+    """The 4-D setting (WENO5, monotone clamp, band stop) with a local rise of
+    the bound along the position axis."""
+    spec = wl.quad_x4(21, 0.3)
+    base = wl.wind_field(spec, 0.3, 0.0, 0, 0.0, 1.0)
+    raised = wl.wind_field(spec, 0.3, 0.6, 0, 3.5, 0.6)
+    kw = dict(tol=1e-4, clamp=1, band=0.5)
+    dts = (oracle.cfl_dt(spec, dfield=base), oracle.cfl_dt(spec, dfield=raised))
+    st0, Wf, full, Wl, loc = local_case(hj, spec, 5, base, raised, 1e-6, dts=dts, **kw)
+    scale = np.abs(Wf).max()
+    assert np.abs(Wl - Wf).max() <= REL * scale, np.abs(Wl - Wf).max()
+    assert sign_agreement_far(Wl, Wf) >= SIGN_FRAC
+    assert loc["stepped"] < 1.0
+    # the oracle runs its own prior to the GPU prior's stop step and its own
+    # warm solve, with full stepping, to the localized solve's stop step, at
+    # the same dt (the GPU's values are never oracle inputs)
+    Wp, _ = oracle.solve(spec, scheme=5, dt=dts[0], dfield=base, clamp=1,
+                         fixed_steps=st0["steps"])
+    Wo, _ = oracle.solve(spec, scheme=5, dt=dts[1], dfield=raised, warm=Wp, clamp=1,
+                         fixed_steps=loc["steps"])
+    assert np.abs(Wl - Wo).max() <= REL * np.abs(Wo).max(), np.abs(Wl - Wo).max()
+    assert sign_agreement_far(Wl, Wo) >= SIGN_FRAC
+
+
+def test_localized_stepping_edges(hj):
+    """Everything quiet: nothing steps after the first window and the solve
+    stops there; fixed-step runs ignore the option; a flat launch shape is
+    switched to row tiles; bad settings are rejected."""
+    spec = wl.quad_z(61, 0.5)
+    g = hj.Grid.from_spec(spec)
+    g.solve(hj.HJ_COLD, scheme=2, tol=1e-6)
+    W0 = g.value()
+    st = g.solve(hj.HJ_WARM, scheme=2, tol=1e-6, local_tol=1e-6)
+    assert st["converged"] and st["windows"] == 1
+    assert np.abs(g.value() - W0).max() < 1e-6
+    assert g.launch_shape()[1] > 0
+    st = g.solve(hj.HJ_WARM, scheme=2, fixed_steps=5, local_tol=1e-6)
+    assert st["steps"] == 5 and st["stepped"] == 1.0
+    with pytest.raises(hj.HJError):
+        g.solve(hj.HJ_WARM, scheme=2, local_tol=-1.0)
+    with pytest.raises(hj.HJError):
+        g.solve(hj.HJ_WARM, scheme=2, local_tol=1e-6, local_margin=-1)
+    g.close()

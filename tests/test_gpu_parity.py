@@ -781,14 +781,17 @@ def test_kernel_launch_counter_moves(hj):
 
 
 def test_autotune_keeps_value_and_results(hj):
-    """The launch-shape autotuner only changes threads per block: W is left
-    as it was, and solves after tuning give bit-identical results."""
+    """The launch-shape autotuner only changes how the stage kernels map onto
+    the GPU (flat block size or row tiles): W is left as it was, and solves
+    after tuning give bit-identical results."""
     spec = wl.quad_x4(23, 0.5)
     g = hj.Grid.from_spec(spec)
     g.solve(hj.HJ_COLD, scheme=5, fixed_steps=3)
     before = g.value()
     t = hj.hj_autotune(g.handle, hj.HJ_WENO5)
     assert t in (128, 256, 512)
+    threads, rows = g.launch_shape()
+    assert threads == t and rows >= 0
     assert np.array_equal(g.value(), before)
     st1 = g.solve(hj.HJ_COLD, scheme=5, fixed_steps=7)
     W1 = g.value()
@@ -831,6 +834,83 @@ def test_shape_specialised_kernels_match_precompiled_bitwise(hj):
         a, b = out[(True, spec.name)], out[(False, spec.name)]
         assert a[2] == b[2]
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def _run_shape(hj, spec, scheme, threads, rows, **kw):
+    g = hj.Grid.from_spec(spec)
+    g.set_launch_shape(threads, rows)
+    assert g.launch_shape() == (threads, rows)
+    g.solve(hj.HJ_COLD, scheme=scheme, fixed_steps=7, **kw)
+    Wf = g.value()
+    st = g.solve(hj.HJ_COLD, scheme=scheme, tol=1e-3, max_steps=300, **kw)
+    Wc = g.value()
+    g.close()
+    return Wf, Wc, st
+
+
+@pytest.mark.parametrize("name,spec,scheme,rows", [
+    ("x4-ragged-weno5", wl.drift((13, 15, 9, 19), 1.0, 0.5), 5, (1, 5, 15, 53)),
+    ("x4-weno5", wl.quad_x4(13, 0.5), 5, (1, 7, 13)),
+    ("z-eno2", wl.quad_z(57, 0.5), 2, (1, 4, 17)),
+    ("z-weno5", wl.quad_z(83, 0.5), 5, (1, 3, 12)),
+    ("drift3-eno2", wl.drift((9, 11, 13), 1.0, 0.4), 2, (1, 9, 78)),
+    ("drift1-weno5", wl.drift((300,), 1.0, 0.3), 5, (1,)),
+    ("drift2-first", wl.drift((40, 31), 1.0, 0.3), 1, (2, 33)),
+], ids=lambda v: v if isinstance(v, str) else "")
+def test_row_tiles_match_flat_mapping_bitwise(hj, name, spec, scheme, rows):
+    """Row tiles (lines of the fastest axis staged in shared memory with
+    their ghost values) compute the same values as the flat one-node-per-
+    thread mapping, bit for bit: fixed steps, and a converged solve (the
+    window residual is reduced per block) with the same step count; for
+    every line count, including tiles whose last one is short, and against
+    the oracle."""
+    Wf0, Wc0, st0 = _run_shape(hj, spec, scheme, 256, 0)
+    for r in rows:
+        Wf, Wc, st = _run_shape(hj, spec, scheme, 256, r)
+        assert np.array_equal(Wf, Wf0), (name, r)
+        assert np.array_equal(Wc, Wc0) and st["steps"] == st0["steps"], (name, r)
+    dt = oracle.cfl_dt(spec)
+    g = hj.Grid.from_spec(spec)
+    g.set_launch_shape(256, rows[-1])
+    g.solve(hj.HJ_COLD, scheme=scheme, dt=dt, fixed_steps=7)
+    Wo, _ = oracle.solve(spec, scheme=scheme, dt=dt, fixed_steps=7)
+    assert_parity(g.value(), Wo, spec)
+    g.close()
+
+
+def test_row_tiles_reject_shapes_that_do_not_fit(hj):
+    g = hj.Grid.from_spec(wl.quad_x4(41, 0.5))
+    with pytest.raises(hj.HJError):
+        g.set_launch_shape(256, 25)  # 1025 nodes per tile
+    with pytest.raises(hj.HJError):
+        g.set_launch_shape(300, 0)
+    g.set_launch_shape(256, 24)
+    g.close()
+
+
+def test_specialised_row_tiles_match_flat_bitwise(hj):
+    """Row tiles compiled at run time for a grid of >= 2^20 nodes, on direct
+    launches and inside captured graphs: the same values as the precompiled
+    flat kernels, bit for bit."""
+    spec = wl.quad_x4(33, 0.5)
+    out = {}
+    try:
+        for jit, rows in ((False, 0), (True, 7), (True, 31)):
+            hj.hj_set_jit(jit)
+            g = hj.Grid.from_spec(spec)
+            g.set_launch_shape(256, rows)
+            g.solve(hj.HJ_COLD, scheme=5, fixed_steps=1, use_graph=False)
+            assert hj.hj_jit_wait(120.0)
+            g.solve(hj.HJ_COLD, scheme=5, fixed_steps=6, use_graph=False)
+            Wd = g.value()
+            st = g.solve(hj.HJ_COLD, scheme=5, tol=1e-2, max_steps=400)
+            out[(jit, rows)] = (Wd, g.value(), st["steps"])
+            g.close()
+    finally:
+        hj.hj_set_jit(True)
+    ref = out[(False, 0)]
+    for k, v in out.items():
+        assert v[2] == ref[2] and np.array_equal(v[0], ref[0]) and np.array_equal(v[1], ref[1]), k
 
 
 def test_exit_with_a_compile_running_is_clean(hj):

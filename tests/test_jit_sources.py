@@ -25,3 +25,24 @@ def test_bad_arguments_are_rejected():
         hj.hj_jit_check([41] * 4, "quad_x4", 5, 300)
     with pytest.raises(hj.HJError):
         hj.hj_jit_check([2, 41], "quad_z", 2, 256)
+
+
+TILE_CASES = ([("quad_x4", [41, 41, 41, 41], s, r) for s in (1, 2, 5) for r in (3, 6, 7)]
+              + [("quad_x4", [81, 81, 81, 81], 5, r) for r in (3, 5, 12)]
+              + [("quad_z", [201, 201], s, r) for s in (2, 5) for r in (1, 2, 5)]
+              + [("drift", n, 5, 2) for n in ([300, 5], [101, 103], [33, 35, 37], [9, 11, 13, 15])])
+
+
+@pytest.mark.parametrize("model,n,scheme,rows", TILE_CASES,
+                         ids=["%s-%dd-s%d-r%d" % (m, len(n), s, r) for m, n, s, r in TILE_CASES])
+def test_specialised_row_tile_source_compiles(model, n, scheme, rows):
+    hj.hj_jit_check_tiles(n, model, scheme, rows)
+
+
+def test_row_tiles_that_do_not_fit_are_rejected():
+    with pytest.raises(hj.HJError):
+        hj.hj_jit_check_tiles([81] * 4, "quad_x4", 5, 13)  # 1053 nodes > 1024
+    with pytest.raises(hj.HJError):
+        hj.hj_jit_check_tiles([300], "drift", 5, 2)  # one line only
+    with pytest.raises(hj.HJError):
+        hj.hj_jit_check_tiles([41] * 4, "quad_x4", 5, 0)
