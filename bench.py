@@ -85,7 +85,12 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-scenarios", action="store_true",
                     help="skip the decomposed / adaptive-grid / serving scenarios")
-    ap.add_argument("--serve-requests", type=int, default=16)
+    ap.add_argument("--serve-requests", type=int, default=256,
+                    help="requests of the seeded serving trace replayed (all 256 by default)")
+    ap.add_argument("--serve-coarse", action="store_true",
+                    help="also replay the trace with coarse initialisation of the 4-D requests")
+    ap.add_argument("--max-wall-ms", type=float, default=300000.0,
+                    help="wall-time cap of each headline solve (0: none; for slow profilers)")
     ap.add_argument("--secondary-steps", type=int, default=3,
                     help="timed steps of the 41^4 cold + warm pair")
     ap.add_argument("--only-headline", action="store_true",
@@ -420,6 +425,7 @@ def profile_only(args, hj, wl):
 
 
 def main():
+    t_start = time.perf_counter()
     args = parse()
     if args.impl == "reference":
         run_reference(args)
@@ -447,7 +453,7 @@ def main():
     cs, fs = wl.quad_x4(N_COARSE, BOUND), wl.quad_x4(N_FINE, BOUND)
     gc = hj.Grid.from_spec(cs, stream=stream)
     gf = hj.Grid.from_spec(fs, stream=stream)
-    opts = dict(scenarios.X4_OPTS)
+    opts = dict(scenarios.X4_OPTS, max_wall_ms=args.max_wall_ms)
     if args.no_graph:
         opts["use_graph"] = False
 
@@ -581,7 +587,9 @@ def main():
                 "localized_update": scenarios.localized_update(),
                 "moving_constraint": scenarios.moving_constraint(),
                 "safety_filter": scenarios.safety_filter(),
-                "serving": scenarios.serving(args.serve_requests)}
+                "serving": scenarios.serving(
+                    args.serve_requests,
+                    forms=("served", "served_coarse_init") if args.serve_coarse else ("served",))}
     if rank != 0:
         return
     latency = {
@@ -626,6 +634,7 @@ def main():
         line["scenarios"] = scen
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
+    line["bench_wall_s"] = time.perf_counter() - t_start
     print(json.dumps(line))
 
 

@@ -110,8 +110,10 @@ typedef struct {
   double local_tol;      /* > 0: localized stepping (Sec. VI): after the first window,    */
                          /* only slabs whose value changed by more than local_tol in the  */
                          /* last window (nodes within band_margin of a free face do not   */
-                         /* count; nodes outside the band do), and slabs within           */
-                         /* local_margin of them, step;                                   */
+                         /* count; nodes outside the band do), and slabs close enough to  */
+                         /* them for a change to arrive within the next window (the CFL   */
+                         /* distance of a window along each slab axis, plus               */
+                         /* local_margin slabs), step;                                    */
                          /* the others keep their value.  Slabs are the lines of the two  */
                          /* slowest axes of a 4-D grid, the first axis of a 2-D or 3-D    */
                          /* grid.  Stage values next to stepping slabs are recomputed on  */
@@ -119,7 +121,7 @@ typedef struct {
                          /* update is the full solve's update of the current field.       */
                          /* Needs row tiles (the launch shape is switched to them if      */
                          /* needed); ignored with fixed_steps.  0 (default): off.         */
-  int local_margin;      /* reactivation margin in slabs (default 2)                      */
+  int local_margin;      /* extra reactivation margin in slabs (default 1)                */
 } hj_solve_opts;
 
 typedef struct {
@@ -521,6 +523,11 @@ long long hj_jit_pending(void);
 hj_status hj_jit_check(int ndim, const int* n, int model, int scheme, int threads);
 /* The same for the row-tile stage kernels of tile_rows lines per block. */
 hj_status hj_jit_check_tiles(int ndim, const int* n, int model, int scheme, int tile_rows);
+/* The same for the group kernels of a batch of ngrids grids (grid k:
+ * ndims[k] axes of shapes[4k..4k+ndims[k]) nodes, models[k], schemes[k]),
+ * the kernels a batch runs once they are compiled for its composition. */
+hj_status hj_jit_check_group(int ngrids, const int* ndims, const int* shapes, const int* models,
+                             const int* schemes);
 
 /* Number of nodes of the grid. */
 long long hj_grid_points(hj_grid g);

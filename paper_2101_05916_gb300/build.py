@@ -21,7 +21,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["hj_kernels.cu", "hj_api.cu", "hj_batch.cu", "hj_server.cu", "hj_static.cu",
            "hj_filter.cu", "hj_jit.cu"]
 # device headers that hj_jit.cu hands to NVRTC as text
-JIT_HEADERS = ["hj_device.cuh", "hj_stage.cuh"]
+JIT_HEADERS = ["hj_device.cuh", "hj_stage.cuh", "hj_group.cuh"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-ftz=true",
          "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC, "-I" + BUILD]
 

@@ -370,10 +370,12 @@ static float bits_to_float(unsigned b) {
 // Localized stepping (hj_solve_opts.local_tol > 0).  Window by window:
 //   - the first window steps every slab;
 //   - after each window a mask kernel turns the per-slab changes into the
-//     slabs that step (changed by more than local_tol, or within
-//     local_margin slabs of one that did) and the rings on which stages 1
-//     and 2 are recomputed (2 and 1 stencil radii further), and a list
-//     kernel turns them into the row tiles of each stage;
+//     slabs that step (changed by more than local_tol, or close enough to
+//     one that did for the change to reach them within the next window:
+//     the CFL distance of a window along each slab axis plus local_margin)
+//     and the rings on which stages 1 and 2 are recomputed (2 and 1
+//     stencil radii further), and a list kernel turns them into the row
+//     tiles of each stage;
 //   - the next window launches exactly those tiles; stage 3 commits only
 //     stepping slabs, the others keep W and their snapshot.
 // The stop test is the usual one over the nodes that step.  One read-back
@@ -412,6 +414,17 @@ hj_status solve_local(hj_grid g, const hj_solve_opts& o, double dt, hj_solve_sta
   const float fdt = (float)dt;
   long long per = (long long)std::ceil(o.check_dt / dt - 1e-9);
   if (per < 1) per = 1;
+  // how far (in slabs) a change can travel along each slab axis in one
+  // window: the CFL speed alpha_a dt / h_a cells per step times the steps,
+  // plus the caller's margin
+  int kax[2] = {0, 0};
+  for (int q = 0; q < 2; ++q) {
+    int ax = q;  // slab axes: 0 and 1 of a 4-D grid, 0 of a 2-D or 3-D grid
+    int slab_axes = g->ndim == 4 ? 2 : (g->ndim >= 2 ? 1 : 0);
+    if (ax >= slab_axes) continue;
+    double cells = (double)per * (double)g->alpha[ax] * dt / g->h[ax];
+    kax[q] = (int)std::ceil(cells) + 1 + o.local_margin;
+  }
   int counts[3] = {L.ntiles, L.ntiles, L.ntiles};
   bool first = true;
   double tiles_run = 0.0, tiles_full = 0.0;
@@ -445,7 +458,7 @@ hj_status solve_local(hj_grid g, const hj_solve_opts& o, double dt, hj_solve_sta
     }
     tiles_run += (double)todo * (counts[0] + counts[1] + counts[2]);
     tiles_full += (double)todo * 3.0 * L.ntiles;
-    HJ_CU(hjk::launch_local_lists(d, o.scheme, g->slab_resid, (float)o.local_tol, o.local_margin,
+    HJ_CU(hjk::launch_local_lists(d, o.scheme, g->slab_resid, (float)o.local_tol, kax[0], kax[1],
                                   g->slab_masks, g->tile_lists, g->tile_counts, s));
     HJ_CU(cudaMemcpyAsync(g->hscal + 4, g->dscal + 4, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     HJ_CU(cudaMemcpyAsync(g->tile_counts_h, g->tile_counts, 3 * sizeof(int),
@@ -501,7 +514,7 @@ void hj_default_opts(hj_solve_opts* o) {
   o->autotune = 0;
   o->band_margin = 0;
   o->local_tol = 0.0;
-  o->local_margin = 2;
+  o->local_margin = 1;
 }
 
 void hj_grid_destroy(hj_grid g) {

@@ -304,6 +304,7 @@ hj_status Runner::rebuild() {
     order_.push_back(k);
   }
   nitems_ = (int)order_.size();
+  plan_group();
   if (nitems_ > item_cap_) {
     cudaFree(dev_slots_);
     dev_slots_ = nullptr;
@@ -320,12 +321,106 @@ hj_status Runner::rebuild() {
   return HJ_OK;
 }
 
+// The group launch of the current membership: every active grid in row
+// tiles of a common block size (the smallest of 256/512/1024 threads that
+// holds a whole line of every grid), each grid with as many lines per tile
+// as fit, and one specialised body per distinct (kind, shape, constants).
+// Group mode is on once the composition's kernels are compiled and loaded.
+bool Runner::plan_group() {
+  // a loaded kernel serves any membership whose codes it holds (grids that
+  // retire from a batch leave a subset)
+  void* keep_handle = group_mode_ ? group_handle_ : nullptr;
+  std::vector<std::string> keep_keys = keep_handle ? gkeys_ : std::vector<std::string>();
+  std::vector<hjd::DevGrid> keep_codes = gcodes_;
+  std::vector<int> keep_schemes = gschemes_;
+  int keep_T = gthreads_, keep_smem = gsmem_;
+  group_mode_ = false;
+  group_pending_ = false;
+  group_handle_ = nullptr;
+  gcodes_.clear();
+  gschemes_.clear();
+  gkeys_.clear();
+  if (!group_allowed_ || nitems_ < 1 || nitems_ > kGroupItems) return false;
+  int maxn = 0;
+  for (int k : order_) maxn = std::max(maxn, slots_[k].g->n[slots_[k].g->ndim - 1]);
+  if (maxn > hjk::kTileMaxThreads) return false;
+  int T = maxn <= 256 ? 256 : (maxn <= 512 ? 512 : 1024);
+  bool reuse = keep_handle && T == keep_T;
+  if (reuse) {
+    gkeys_ = keep_keys;
+    gcodes_ = keep_codes;
+    gschemes_ = keep_schemes;
+  }
+  std::memset(&gpack_, 0, sizeof(gpack_));
+  std::vector<std::string>& keys = gkeys_;
+  unsigned blocks = 0;
+  int smem = 0;
+  for (int i = 0; i < nitems_; ++i) {
+    int k = order_[i];
+    const Slot& s = slots_[k];
+    hj_grid g = s.g;
+    hjd::DevGrid d = hja::devgrid(g);
+    int n = d.n[d.ndim - 1];
+    d.tile_rows = std::max(1, std::min(T / n, d.nrows));
+    const void* f[3] = {g->W, g->A, g->B};
+    if (!hjk::tile_ok(d, d.tile_rows, f, 3)) return false;
+    std::string key = hjk::code_key(d, s.scheme);
+    int code = -1;
+    for (size_t c = 0; c < keys.size(); ++c)
+      if (keys[c] == key) code = (int)c;
+    if (code < 0) {
+      reuse = false;
+      code = (int)keys.size();
+      keys.push_back(key);
+      gcodes_.push_back(d);
+      gschemes_.push_back(s.scheme);
+    }
+    int radius = s.scheme == 5 ? 3 : (s.scheme == 2 ? 2 : 1);
+    smem = std::max(smem, d.tile_rows * (n + 2 * radius));
+    GroupItem& it = gpack_.items[i];
+    it.g = d;
+    float dt = (float)s.dt;
+    it.a[0] = hjd::StageArgs{g->W, g->W, g->A, nullptr, nullptr, dt, 0, s.clamp, s.band, s.margin};
+    it.a[1] = hjd::StageArgs{g->A, g->W, g->B, nullptr, nullptr, dt, 0, s.clamp, s.band, s.margin};
+    it.a[2] = hjd::StageArgs{g->B, g->W, g->W, g->snap, nullptr, dt, 0, s.clamp, s.band, s.margin};
+    it.slot = k;
+    it.code = code;
+    gpack_.block_begin[i] = (int)blocks;
+    blocks += (unsigned)((d.nrows + d.tile_rows - 1) / d.tile_rows);
+  }
+  gpack_.count = nitems_;
+  gpack_.block_begin[nitems_] = (int)blocks;
+  gblocks_ = blocks;
+  gthreads_ = T;
+  if (reuse && smem <= keep_smem) {
+    gsmem_ = keep_smem;
+    group_handle_ = keep_handle;
+    group_mode_ = true;
+    return true;
+  }
+  gsmem_ = smem;
+  group_mode_ = hjk::group_prepare(gcodes_, gschemes_, gthreads_, gsmem_, &group_handle_);
+  group_pending_ = !group_mode_ && hjk::jit_enabled();
+  return group_mode_;
+}
+
 // R steps: per step, the three stage launches of every kind group, then the
 // control kernel over all grids.  A group holding a single grid uses the
 // single-grid kernel, whose descriptor is a plain kernel parameter.  Rounds
 // end at the first window boundary of any grid, so such a grid can check only
 // at the round's last step, and only when its own window ends there.
 cudaError_t Runner::enqueue_round(long long R, cudaStream_t s) {
+  if (group_mode_) {
+    for (long long i = 0; i < R; ++i) {
+      for (int stage = 1; stage <= 3; ++stage) {
+        cudaError_t e = hjk::group_launch(group_handle_, stage, &gpack_, dev_ctl_, gblocks_,
+                                          gthreads_, s);
+        if (e != cudaSuccess) return e;
+      }
+      batch_control<<<1, 256, 0, s>>>(dev_slots_, nitems_, dev_ctl_);
+    }
+    return cudaGetLastError();
+  }
   for (long long i = 0; i < R; ++i) {
     for (int stage = 1; stage <= 3; ++stage) {
       for (const Group& gr : groups_) {
@@ -368,6 +463,14 @@ hj_status Runner::sync_ctl() {
 hj_status Runner::round(bool use_graph) {
   hja::DeviceGuard dg(device_);
   hj_status st;
+  // the group kernels of the current membership finished compiling: switch
+  if (!dirty_ && group_pending_ && !group_mode_) {
+    group_mode_ = hjk::group_prepare(gcodes_, gschemes_, gthreads_, gsmem_, &group_handle_);
+    if (group_mode_) {
+      group_pending_ = false;
+      drop_graphs();
+    }
+  }
   bool changed = dirty_;
   if (dirty_ && (st = rebuild()) != HJ_OK) return st;
   if (nitems_ == 0) return HJ_OK;
@@ -390,8 +493,10 @@ hj_status Runner::round(bool use_graph) {
   R = std::max(1ll, std::min(R, std::min(r_work, 4096ll)));
   // a single-grid group bakes its check step into the launch, so the graph
   // key holds each such grid's phase within its window
-  std::string key = std::to_string(R);
-  for (const Group& gr : groups_)
+  std::string key = std::to_string(R) + (group_mode_ ? "G" : "");
+  static const std::vector<Group> kNoGroups;
+  const std::vector<Group>& solo = group_mode_ ? kNoGroups : groups_;
+  for (const Group& gr : solo)
     if (gr.pack.count == 1) {
       const Ctl& c = host_ctl_[gr.pack.items[0].slot];
       long long to_cap = c.max_steps - c.steps;
@@ -399,7 +504,7 @@ hj_status Runner::round(bool use_graph) {
     }
   // grids launched on their own may use shape-specialised kernels: they
   // load outside the capture, and a round graph records whether it has them
-  for (const Group& gr : groups_)
+  for (const Group& gr : solo)
     if (gr.pack.count == 1)
       key += hjk::jit_prepare(gr.pack.items[0].g, gr.pack.items[0].kind % 10,
                               slots_[gr.pack.items[0].slot].g->threads)
@@ -432,7 +537,8 @@ hj_status Runner::round(bool use_graph) {
   // every kernel of the round counted once: single-grid launches counted
   // themselves while enqueued (also during capture), so top up to the total
   unsigned long long counted = hjk::g_launches.load() - before;
-  unsigned long long total = (3ull * groups_.size() + 1ull) * (unsigned long long)R;
+  unsigned long long total =
+      (3ull * (group_mode_ ? 1ull : groups_.size()) + 1ull) * (unsigned long long)R;
   if (total > counted) hjk::g_launches.fetch_add(total - counted);
   if ((st = sync_ctl()) != HJ_OK) return st;
   // wall-time caps are host-side and apply between rounds
@@ -494,6 +600,7 @@ extern "C" hj_status hj_solve_batch(hj_grid* gs, int ngrids, const int* modes,
       if (gs[j] == gs[i]) return hja::fail(HJ_ERR_ARG, "grid %d appears twice", i);
   }
   hjb::Runner r(gs[0]->device, gs[0]->stream, std::max(ngrids, 1));
+  r.allow_group(true);
   hj_status st = r.init();
   if (st != HJ_OK) return st;
   std::vector<int> slot(ngrids, -1);

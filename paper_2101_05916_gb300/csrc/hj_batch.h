@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "hj_grid.h"
+#include "hj_group.cuh"
 
 namespace hjb {
 
@@ -32,18 +33,7 @@ struct ItemPack {
 };
 static_assert(sizeof(ItemPack) <= 32000, "kernel parameters are limited to 32764 bytes");
 
-// Per-grid stepping state, written only by the control kernel between steps.
-struct Ctl {
-  int active;         // 1 while the grid is stepping
-  int status;         // 0 running, 1 converged, 2 step cap, 3 non-finite, 4 cancelled
-  long long per;      // steps per check window
-  long long steps;    // steps done
-  long long max_steps;
-  long long windows;
-  double tol;         // stop when the window residual drops below (negative: never)
-  unsigned resid;     // running window residual (float bits)
-  float last_resid;
-};
+static_assert(sizeof(GroupPack) <= 32000, "kernel parameters are limited to 32764 bytes");
 
 enum { S_RUNNING = 0, S_CONVERGED = 1, S_CAP = 2, S_NONFINITE = 3, S_CANCELLED = 4 };
 
@@ -67,6 +57,14 @@ class Runner {
   // Final state of a finished slot; frees the slot for reuse.
   hj_status collect(int slot, hj_solve_stats* st);
   long long steps_of(int slot) const { return host_ctl_[slot].steps; }
+  // Allow group launches (one launch per stage over all grids, compiled per
+  // membership).  Worth it for a membership that steps many rounds, as in
+  // hj_solve_batch; a server whose membership changes every few rounds
+  // would only start compiles it never uses.  Off by default.
+  void allow_group(bool on) {
+    group_allowed_ = on;
+    dirty_ = true;
+  }
   cudaStream_t stream() const { return stream_; }
 
  private:
@@ -104,6 +102,20 @@ class Runner {
   std::vector<int> order_;  // slots in the current item list
   std::map<std::string, cudaGraphExec_t> graphs_;  // round shape -> graph
   cudaStream_t cap_stream_ = nullptr;
+  // Group mode: one launch per RK stage over the row tiles of every active
+  // grid, with the kernels compiled for this composition (hj_group.cuh).
+  // Until they are compiled the per-kind launches above run.
+  bool group_allowed_ = false;
+  bool group_mode_ = false;
+  bool group_pending_ = false;  // a compile of the current composition is running
+  void* group_handle_ = nullptr;
+  GroupPack gpack_;
+  unsigned gblocks_ = 0;
+  int gthreads_ = 0, gsmem_ = 0;
+  std::vector<hjd::DevGrid> gcodes_;
+  std::vector<int> gschemes_;
+  std::vector<std::string> gkeys_;  // code keys of the kernels in group_handle_
+  bool plan_group();
 };
 
 }  // namespace hjb

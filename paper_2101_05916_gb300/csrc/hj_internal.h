@@ -3,6 +3,8 @@
 #pragma once
 
 #include <atomic>
+#include <string>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "hj_device.cuh"
@@ -38,9 +40,11 @@ struct LocalLayout {
 LocalLayout local_layout(const hjd::DevGrid& g);
 // From the window's per-slab changes (float bits, nslabs entries): the slab
 // masks (3 x nslabs bytes: live, ring2, ring1) and the row-tile lists of the
-// three stages (3 x ntiles ints) with their lengths in counts[0..2].
+// three stages (3 x ntiles ints) with their lengths in counts[0..2].  A
+// slab steps when one that changed by more than thr lies within k0 slabs
+// along the first slab axis and k1 along the second.
 cudaError_t launch_local_lists(const hjd::DevGrid& g, int scheme, const unsigned* slab_resid,
-                               float thr, int margin, unsigned char* masks, int* lists,
+                               float thr, int k0, int k1, unsigned char* masks, int* lists,
                                int* counts, cudaStream_t s);
 
 // Streaming multiprocessors of the current device (read once per device).
@@ -66,6 +70,21 @@ bool jit_wanted(const hjd::DevGrid& g);
 bool jit_prepare(const hjd::DevGrid& g, int scheme, int threads);
 cudaError_t jit_launch(const hjd::DevGrid& g, int scheme, int stage, const hjd::StageArgs& a,
                        cudaStream_t s, int threads, bool* used);
+// Group kernels of a batch (hj_group.cuh): codes[c] is a representative
+// grid descriptor (row tiles set) of code c, run with schemes[c]; threads per
+// block and shared floats per block are common to all codes.  The first
+// sight of a composition starts its background compile; true (and *handle)
+// once it is loaded.  Must not be called inside a stream capture.
+bool group_prepare(const std::vector<hjd::DevGrid>& codes, const std::vector<int>& schemes,
+                   int threads, int smem_floats, void** handle);
+// One group launch of stage 1..3 over `blocks` blocks; pack points at a
+// hjb::GroupPack, ctl is the device control array.
+cudaError_t group_launch(void* handle, int stage, const void* pack, void* ctl, unsigned blocks,
+                         int threads, cudaStream_t s);
+// Identity of a grid's specialised code: kind, shape, geometry, model
+// constants, constraint kind and tile height (the folded fields).
+std::string code_key(const hjd::DevGrid& g, int scheme);
+bool jit_enabled();
 long long jit_compiled();
 long long jit_pending();
 void jit_enable(int on);

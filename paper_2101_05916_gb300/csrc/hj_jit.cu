@@ -29,6 +29,7 @@
 #include "hj.h"
 #include "hj_grid.h"
 #include "hj_internal.h"
+#include "hj_group.cuh"
 
 // kJitHeaderNames / kJitHeaders: the device headers as text (build.py)
 #include "hj_jit_sources.inc"
@@ -149,12 +150,11 @@ Key key_of(const hjd::DevGrid& g, int scheme, int threads) {
   return k;
 }
 
-// The stage kernels of stage_kernel (hj_kernels.cu) with the shape fields
-// of the grid descriptor replaced by literals.
-std::string source(const hjd::DevGrid& g, int scheme, int threads) {
-  std::string s = "#include \"hj_stage.cuh\"\n";
-  s += "__device__ __forceinline__ hjd::DevGrid hj_fixed(const hjd::DevGrid& g) {\n";
-  s += "  hjd::DevGrid c = g;\n";
+// A device function `name` that returns the grid descriptor with its shape,
+// geometry, model constants and constraint kind replaced by literals.
+std::string fixed_fn(const std::string& name, const hjd::DevGrid& g) {
+  std::string s = "__device__ __forceinline__ hjd::DevGrid " + name +
+                  "(const hjd::DevGrid& g) {\n  hjd::DevGrid c = g;\n";
   char buf[256];
   for (int d = 0; d < g.ndim; ++d) {
     std::snprintf(buf, sizeof(buf), "  c.n[%d] = %d; c.stride[%d] = %d;\n", d, g.n[d], d,
@@ -178,10 +178,21 @@ std::string source(const hjd::DevGrid& g, int scheme, int threads) {
                 g.npts, g.plane, g.nrows, g.tile_rows, g.div_m[0], g.div_s[0], g.div_m[1],
                 g.div_s[1], g.div_m[2], g.div_s[2]);
   s += buf;
+  return s;
+}
+
+int radius_of(int scheme) { return scheme == 5 ? 3 : (scheme == 2 ? 2 : 1); }
+
+// The stage kernels of stage_kernel (hj_kernels.cu) with the shape fields
+// of the grid descriptor replaced by literals.
+std::string source(const hjd::DevGrid& g, int scheme, int threads) {
+  std::string s = "#include \"hj_stage.cuh\"\n";
+  s += fixed_fn("hj_fixed", g);
+  char buf[256];
   if (g.tile_rows > 0) {
     // row tiles: the tile's shared memory is a static array of its exact size
     TileShape ts = tile_shape(g, scheme);
-    int pitch = g.n[g.ndim - 1] + 2 * (scheme == 5 ? 3 : (scheme == 2 ? 2 : 1));
+    int pitch = g.n[g.ndim - 1] + 2 * radius_of(scheme);
     for (int st = 1; st <= 3; ++st) {
       std::snprintf(buf, sizeof(buf),
                     "extern \"C\" __global__ void __launch_bounds__(%d)\n"
@@ -209,6 +220,41 @@ std::string source(const hjd::DevGrid& g, int scheme, int threads) {
     if (st == 3) s += "  if (a.check) hjd::block_max_bits(r, a.resid);\n";
     else s += "  (void)r;\n";
     s += "}\n";
+  }
+  return s;
+}
+
+// The group kernels of a batch: one kernel per RK stage over the row tiles
+// of every grid in a hjb::GroupPack.  Each distinct (kind, shape, model
+// constants) is one `code` with its own specialised body; a block finds its
+// grid, returns if that grid no longer steps, and runs the body of its code.
+std::string group_source(const std::vector<hjd::DevGrid>& codes, const std::vector<int>& schemes,
+                         int threads, int smem_floats) {
+  std::string s = "#include \"hj_group.cuh\"\n";
+  for (size_t c = 0; c < codes.size(); ++c) s += fixed_fn("hj_fixed_" + std::to_string(c), codes[c]);
+  char buf[512];
+  for (int st = 1; st <= 3; ++st) {
+    std::snprintf(buf, sizeof(buf),
+                  "extern \"C\" __global__ void __launch_bounds__(%d)\n"
+                  "hj_group_%d(const __grid_constant__ hjb::GroupPack pack, hjb::Ctl* ctl) {\n"
+                  "  __shared__ float sm[%d];\n"
+                  "  hjd::StageArgs a;\n  int tile;\n  bool check;\n"
+                  "  int k = hjb::group_find<%d>(pack, ctl, a, tile, check);\n"
+                  "  if (k < 0) return;\n"
+                  "  switch (pack.items[k].code) {\n",
+                  threads, st, smem_floats, st);
+    s += buf;
+    for (size_t c = 0; c < codes.size(); ++c) {
+      std::snprintf(buf, sizeof(buf),
+                    "    case %d: {\n"
+                    "      hjd::TileOut o = hjd::stage_tile<%d, %d, %d, %d>(hj_fixed_%d(pack.items[k].g),"
+                    " a, tile, check, sm);\n"
+                    "      %s\n      break;\n    }\n",
+                    (int)c, codes[c].ndim, schemes[c], codes[c].model, st, (int)c,
+                    st == 3 ? "if (check) hjd::block_max_bits(o.resid, a.resid);" : "(void)o;");
+      s += buf;
+    }
+    s += "  }\n}\n";
   }
   return s;
 }
@@ -279,7 +325,7 @@ void compile_async(std::shared_ptr<Entry> e, std::string src) {
 }
 
 // Load a compiled set on this thread (never inside a capture).
-void load(Entry& e) {
+void load(Entry& e, const char* prefix = "hj_stage_") {
   if (cudaLibraryLoadData(&e.lib, e.cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0) !=
       cudaSuccess) {
     cudaGetLastError();
@@ -289,7 +335,7 @@ void load(Entry& e) {
   }
   for (int st = 0; st < 3; ++st) {
     char name[32];
-    std::snprintf(name, sizeof(name), "hj_stage_%d", st + 1);
+    std::snprintf(name, sizeof(name), "%s%d", prefix, st + 1);
     if (cudaLibraryGetKernel(&e.stage[st], e.lib, name) != cudaSuccess) {
       cudaGetLastError();
       cudaLibraryUnload(e.lib);
@@ -341,7 +387,64 @@ Entry* lookup(const hjd::DevGrid& g, int scheme, int threads, bool may_load) {
   return st == 2 ? e.get() : nullptr;
 }
 
+std::map<std::string, std::shared_ptr<Entry>> g_group_cache;
+
 }  // namespace
+
+bool group_prepare(const std::vector<hjd::DevGrid>& codes, const std::vector<int>& schemes,
+                   int threads, int smem_floats, void** handle) {
+  *handle = nullptr;
+  if (!enabled() || codes.empty()) return false;
+  std::string key = std::to_string(threads) + "/" + std::to_string(smem_floats);
+  for (size_t c = 0; c < codes.size(); ++c) {
+    Key k = key_of(codes[c], schemes[c], threads);
+    key.append(reinterpret_cast<const char*>(&k), sizeof(k));
+  }
+  std::shared_ptr<Entry> e;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_group_cache.find(key);
+    if (it == g_group_cache.end()) {
+      e = std::make_shared<Entry>();
+      g_group_cache.emplace(key, e);
+      if (!nvrtc().ok) {
+        e->state.store(3);
+        return false;
+      }
+      compile_async(e, group_source(codes, schemes, threads, smem_floats));
+      return false;
+    }
+    e = it->second;
+  }
+  int st = e->state.load();
+  if (st == 1) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (e->state.load() == 1) load(*e, "hj_group_");
+    st = e->state.load();
+  }
+  if (st != 2) return false;
+  *handle = e.get();
+  return true;
+}
+
+cudaError_t group_launch(void* handle, int stage, const void* pack, void* ctl, unsigned blocks,
+                         int threads, cudaStream_t s) {
+  Entry* e = static_cast<Entry*>(handle);
+  void* ctlp = ctl;
+  void* args[] = {const_cast<void*>(pack), (void*)&ctlp};
+  cudaError_t err = cudaLaunchKernel((const void*)e->stage[stage - 1], dim3(blocks, 1, 1),
+                                     dim3(threads, 1, 1), args, 0, s);
+  if (err == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
+  return err;
+}
+
+std::string code_key(const hjd::DevGrid& g, int scheme) {
+  Key k = key_of(g, scheme, 0);
+  k.device = 0;
+  return std::string(reinterpret_cast<const char*>(&k), sizeof(k));
+}
+
+bool jit_enabled() { return enabled(); }
 
 bool jit_wanted(const hjd::DevGrid& g) {
   return (long long)g.npts >= kJitNodes && enabled();
@@ -434,6 +537,54 @@ static hj_status jit_check(int ndim, const int* n, int model, int scheme, int th
   if (!hjk::nvrtc().ok) return hja::fail(HJ_ERR_CUDA, "NVRTC could not be loaded");
   std::string log;
   std::vector<char> cubin = hjk::compile(hjk::source(d, scheme, threads), &log);
+  if (cubin.empty()) return hja::fail(HJ_ERR_CUDA, "NVRTC: %.400s", log.c_str());
+  return HJ_OK;
+}
+
+extern "C" hj_status hj_jit_check_group(int ngrids, const int* ndims, const int* shapes,
+                                        const int* models, const int* schemes) {
+  if (ngrids < 1 || ngrids > hjb::kGroupItems || !ndims || !shapes || !models || !schemes)
+    return hja::fail(HJ_ERR_ARG, "bad group description");
+  std::vector<hjd::DevGrid> codes;
+  std::vector<int> sch;
+  int maxn = 0;
+  for (int k = 0; k < ngrids; ++k) maxn = std::max(maxn, shapes[4 * k + ndims[k] - 1]);
+  if (maxn > hjk::kTileMaxThreads) return hja::fail(HJ_ERR_ARG, "a line is longer than a tile");
+  int T = maxn <= 256 ? 256 : (maxn <= 512 ? 512 : 1024);
+  int smem = 0;
+  for (int k = 0; k < ngrids; ++k) {
+    int nd = ndims[k];
+    if (nd < 1 || nd > HJ_MAX_DIM) return hja::fail(HJ_ERR_ARG, "bad ndim");
+    hj_grid_s g;
+    g.ndim = nd;
+    long long npts = 1;
+    for (int i = 0; i < nd; ++i) {
+      int n = shapes[4 * k + i];
+      if (n < 3) return hja::fail(HJ_ERR_ARG, "axis with fewer than 3 nodes");
+      g.n[i] = n;
+      g.lo[i] = 0.0;
+      g.hi[i] = 1.0;
+      g.h[i] = 1.0 / (double)(n - 1);
+      g.ca[i] = 0.25;
+      g.cb[i] = 0.75;
+      npts *= n;
+    }
+    g.npts = npts;
+    g.model = models[k];
+    g.con_kind = hjd::C_BOX;
+    if (!hjk::stage_supported(models[k], nd, schemes[k]))
+      return hja::fail(HJ_ERR_ARG, "model %d, %d-D, scheme %d has no stencil", models[k], nd,
+                       schemes[k]);
+    hjd::DevGrid d = hja::devgrid(&g);
+    int n = d.n[nd - 1];
+    d.tile_rows = std::max(1, std::min(T / n, d.nrows));
+    smem = std::max(smem, d.tile_rows * (n + 2 * hjk::radius_of(schemes[k])));
+    codes.push_back(d);
+    sch.push_back(schemes[k]);
+  }
+  if (!hjk::nvrtc().ok) return hja::fail(HJ_ERR_CUDA, "NVRTC could not be loaded");
+  std::string log;
+  std::vector<char> cubin = hjk::compile(hjk::group_source(codes, sch, T, smem), &log);
   if (cubin.empty()) return hja::fail(HJ_ERR_CUDA, "NVRTC: %.400s", log.c_str());
   return HJ_OK;
 }

@@ -371,31 +371,37 @@ cudaError_t launch_prolong(const DevGrid& c, const float* Wc, const DevGrid& f, 
 // ------------------------------------------------- localized stepping
 
 // Slab masks from the last window's per-slab changes.  A slab is raw-active
-// when its change exceeds thr.  With d the Chebyshev distance (in slabs,
-// over the s0 x s1 slab lattice) to the nearest raw-active slab:
-//   live  (d <= k):      steps and commits its nodes;
-//   ring2 (d <= k + R):  stage 2 is computed there, so that stage 3 at live
-//                        nodes reads valid W2 within its stencil radius R;
-//   ring1 (d <= k + 2R): stage 1 is computed there, so that stage 2 on ring2
-//                        reads valid W1.
-// k is the reactivation margin: a frozen slab wakes up when a slab within k
-// of it changed by more than thr in the last window.
+// when its change exceeds thr.  A slab
+//   steps (live)          when a raw-active slab lies within k0 slabs along
+//                         the first slab axis and k1 along the second;
+//   gets stage 2 (ring2)  within k0 + R, k1 + R, so that stage 3 at live
+//                         nodes reads valid W2 within its stencil radius R;
+//   gets stage 1 (ring1)  within k0 + 2R, k1 + 2R, so that stage 2 on ring2
+//                         reads valid W1.
+// k0, k1 cover how far a change can travel in one window (the host derives
+// them from the CFL speeds), so that a frozen slab wakes up before anything
+// reaches it.
 __global__ void local_masks_kernel(const unsigned* __restrict__ resid, int s0, int s1, float thr,
-                                   int k, int radius, unsigned char* live, unsigned char* ring2,
-                                   unsigned char* ring1) {
+                                   int k0, int k1, int radius, unsigned char* live,
+                                   unsigned char* ring2, unsigned char* ring1) {
   int sl = blockIdx.x * blockDim.x + threadIdx.x;
   if (sl >= s0 * s1) return;
   int i = sl / s1, j = sl - i * s1;
-  int reach = k + 2 * radius;
-  int best = reach + 1;
-  int i_lo = max(0, i - reach), i_hi = min(s0 - 1, i + reach);
-  int j_lo = max(0, j - reach), j_hi = min(s1 - 1, j + reach);
+  int r0 = k0 + 2 * radius, r1 = k1 + 2 * radius;
+  bool m_live = false, m2 = false, m1 = false;
+  int i_lo = max(0, i - r0), i_hi = min(s0 - 1, i + r0);
+  int j_lo = max(0, j - r1), j_hi = min(s1 - 1, j + r1);
   for (int a = i_lo; a <= i_hi; ++a)
     for (int b = j_lo; b <= j_hi; ++b)
-      if (__uint_as_float(resid[a * s1 + b]) > thr) best = min(best, max(abs(a - i), abs(b - j)));
-  live[sl] = best <= k;
-  ring2[sl] = best <= k + radius;
-  ring1[sl] = best <= k + 2 * radius;
+      if (__uint_as_float(resid[a * s1 + b]) > thr) {
+        int di = abs(a - i), dj = abs(b - j);
+        m1 = true;
+        m2 = m2 || (di <= k0 + radius && dj <= k1 + radius);
+        m_live = m_live || (di <= k0 && dj <= k1);
+      }
+  live[sl] = m_live;
+  ring2[sl] = m2;
+  ring1[sl] = m1;
 }
 
 // Tile lists of the next window: list q (q = 0, 1, 2 for stages 1, 2, 3)
@@ -443,15 +449,16 @@ LocalLayout local_layout(const DevGrid& g) {
 }
 
 cudaError_t launch_local_lists(const DevGrid& g, int scheme, const unsigned* slab_resid,
-                               float thr, int margin, unsigned char* masks, int* lists,
+                               float thr, int k0, int k1, unsigned char* masks, int* lists,
                                int* counts, cudaStream_t s) {
   LocalLayout L = local_layout(g);
   int radius = scheme == 5 ? 3 : (scheme == 2 ? 2 : 1);
   unsigned char *live = masks, *ring2 = masks + L.nslabs, *ring1 = masks + 2 * L.nslabs;
   cudaError_t e = cudaMemsetAsync(counts, 0, 3 * sizeof(int), s);
   if (e != cudaSuccess) return e;
-  local_masks_kernel<<<(L.nslabs + 255) / 256, 256, 0, s>>>(slab_resid, L.s0, L.s1, thr, margin,
-                                                           radius, live, ring2, ring1);
+  local_masks_kernel<<<(L.nslabs + 255) / 256, 256, 0, s>>>(slab_resid, L.s0, L.s1, thr, k0,
+                                                           L.s1 > 1 ? k1 : 0, radius, live,
+                                                           ring2, ring1);
   local_lists_kernel<<<(L.ntiles + 255) / 256, 256, 0, s>>>(L.ntiles, g.tile_rows, g.nrows,
                                                            L.rows_per_slab, ring1, ring2, live,
                                                            lists, counts);

@@ -106,6 +106,7 @@ SIGNATURES = {
     "hj_jit_pending": (_ll, []),
     "hj_jit_check": (_i, [_i, _P(_i), _i, _i, _i]),
     "hj_jit_check_tiles": (_i, [_i, _P(_i), _i, _i, _i]),
+    "hj_jit_check_group": (_i, [_i, _P(_i), _P(_i), _P(_i), _P(_i)]),
     "hj_set_launch_shape": (_i, [_vp, _i, _i]),
     "hj_get_launch_shape": (_i, [_vp, _P(_i), _P(_i)]),
     "hj_set_value": (_i, [_vp, _vp, _i]),
@@ -266,7 +267,7 @@ def make_opts(scheme: int = HJ_WENO5, cfl: float = 0.5, dt: float = 0.0, tol: fl
               max_wall_ms: float = 0.0, clamp: int = HJ_CLAMP_VI,
               use_graph: bool = True, band: float = 0.0,
               autotune: bool = False, band_margin: int = 0, local_tol: float = 0.0,
-              local_margin: int = 2) -> hj_solve_opts:
+              local_margin: int = 1) -> hj_solve_opts:
     return hj_solve_opts(scheme, cfl, dt, tol, check_dt, max_steps, fixed_steps, max_wall_ms,
                          clamp, 1 if use_graph else 0, band, 1 if autotune else 0, band_margin,
                          local_tol, local_margin)
@@ -425,6 +426,20 @@ def hj_jit_check_tiles(n: Sequence[int], model, scheme: int, tile_rows: int) -> 
     m = MODELS[model] if isinstance(model, str) else int(model)
     arr = (_i * len(n))(*[int(v) for v in n])
     _check(lib().hj_jit_check_tiles(len(n), arr, m, int(scheme), int(tile_rows)))
+
+
+def hj_jit_check_group(grids) -> None:
+    """Compile the group kernels of a batch with NVRTC (no device needed);
+    grids: a list of (shape, model, scheme)."""
+    k = len(grids)
+    nd = (_i * k)(*[len(sh) for sh, _, _ in grids])
+    shapes = (_i * (4 * k))()
+    for j, (sh, _, _) in enumerate(grids):
+        for i, v in enumerate(sh):
+            shapes[4 * j + i] = int(v)
+    models = (_i * k)(*[MODELS[m] if isinstance(m, str) else int(m) for _, m, _ in grids])
+    schemes = (_i * k)(*[int(s) for _, _, s in grids])
+    _check(lib().hj_jit_check_group(k, nd, shapes, models, schemes))
 
 
 def hj_set_launch_shape(g: int, threads: int = 256, tile_rows: int = 0) -> None:

@@ -355,7 +355,7 @@ X4_EXACT_OPTS = dict(scheme=hj.HJ_WENO5, clamp=hj.HJ_CLAMP_VI, band=0.5, band_ma
                      max_steps=200000, max_wall_ms=300000.0)
 
 
-def localized_update(n4: int = 61, base: float = 0.5, local_tol: float = 1e-5,
+def localized_update(n4: int = 61, base: float = 0.5, local_tol: float = 1e-6,
                      bumps: Sequence[tuple] = ((0.5, 3.0, 0.6), (0.5, -2.5, 0.6),
                                                (0.8, 3.2, 0.4))) -> Dict:
     """Localized warm starting (Sec. VI) on the exact 4-D setting: the wind

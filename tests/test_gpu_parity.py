@@ -511,6 +511,41 @@ def test_batch_equals_single_grid_bitwise(hj):
         g.close()
 
 
+def test_group_launch_is_one_launch_per_stage_and_bitwise_equal(hj):
+    """Once the group kernels of a batch's composition are compiled, every
+    RK stage of every active grid, whatever its kind, is one launch (plus
+    one control launch per step), and each grid still ends bit-identical to
+    its own single-grid solve: fixed steps and to convergence."""
+    specs = [wl.quad_x4(17, 0.5, 4.0, "x"), wl.quad_x4(17, 0.5, 3.5, "y"), wl.quad_z(61, 0.5),
+             wl.quad_x4(13, 0.3)]
+    schemes = [5, 5, 2, 5]
+    grids = [hj.Grid.from_spec(s) for s in specs]
+    opts = [hj.make_opts(scheme=sc, fixed_steps=2) for sc in schemes]
+    hj.hj_solve_batch([g.handle for g in grids], [0] * 4, opts)  # starts the group compile
+    assert hj.hj_jit_wait(120.0)
+    for fixed in (37, 0):
+        singles = []
+        for s, sc in zip(specs, schemes):
+            g = hj.Grid.from_spec(s)
+            st = g.solve(hj.HJ_COLD, scheme=sc, fixed_steps=fixed, tol=1e-4, max_steps=3000)
+            singles.append((g.value(), st))
+            g.close()
+        opts = [hj.make_opts(scheme=sc, fixed_steps=fixed, tol=1e-4, max_steps=3000)
+                for sc in schemes]
+        before = hj.hj_kernel_launches()
+        rc, statuses, stats = hj.hj_solve_batch([g.handle for g in grids], [0] * 4, opts)
+        launches = hj.hj_kernel_launches() - before
+        assert all(st == 0 for st in statuses)
+        if fixed:
+            # 4 inits, then 3 group launches and 1 control launch per step
+            assert launches == 4 + 4 * fixed, launches
+        for g, (Ws, sts), stb in zip(grids, singles, stats):
+            assert stb["steps"] == sts["steps"]
+            assert np.array_equal(g.value(), Ws)
+    for g in grids:
+        g.close()
+
+
 def test_x_and_y_identical_inputs_identical_results(hj):
     s = wl.quad_x4(15, 0.5, 3.5)
     a, b = hj.Grid.from_spec(s), hj.Grid.from_spec(s)

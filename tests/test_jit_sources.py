@@ -46,3 +46,22 @@ def test_row_tiles_that_do_not_fit_are_rejected():
         hj.hj_jit_check_tiles([300], "drift", 5, 2)  # one line only
     with pytest.raises(hj.HJError):
         hj.hj_jit_check_tiles([41] * 4, "quad_x4", 5, 0)
+
+
+GROUPS = [
+    [((61, 61, 61, 61), "quad_x4", 5), ((61, 61, 61, 61), "quad_x4", 5), ((201, 201), "quad_z", 2)],
+    [((31, 31, 31, 31), "quad_x4", 5), ((101, 101), "quad_z", 2), ((401, 401), "quad_z", 2)],
+    [((13, 15, 9, 19), "drift", 2), ((300,), "drift", 5), ((40, 31), "drift", 1)],
+]
+
+
+@pytest.mark.parametrize("grids", GROUPS, ids=["decomposed", "serving-mix", "drift-mix"])
+def test_group_kernel_source_compiles(grids):
+    hj.hj_jit_check_group(grids)
+
+
+def test_group_kernel_bad_arguments_are_rejected():
+    with pytest.raises(hj.HJError):
+        hj.hj_jit_check_group([((5, 2000), "drift", 2)])  # a line longer than any tile
+    with pytest.raises(hj.HJError):
+        hj.hj_jit_check_group([((41, 41), "quad_x4", 5)])  # no such stencil
