@@ -119,8 +119,7 @@ typedef struct {
                          /* grid.  Stage values next to stepping slabs are recomputed on  */
                          /* rings of 1 and 2 stencil radii, so that every stepping node's */
                          /* update is the full solve's update of the current field.       */
-                         /* Needs row tiles (the launch shape is switched to them if      */
-                         /* needed); ignored with fixed_steps.  0 (default): off.         */
+                         /* Ignored with fixed_steps.  0 (default): off.                  */
   int local_margin;      /* extra reactivation margin in slabs (default 1)                */
 } hj_solve_opts;
 
@@ -297,7 +296,9 @@ hj_status hj_alpha(hj_grid g, double* alpha_out);
  *     (Sec. III-B) only when the prior provably dominates the new fixed
  *     point.  That needs the same grid and model, every disturbance
  *     interval of the prior inside the new one, and the prior's constraint
- *     box containing the new one.  Otherwise the request solves cold.
+ *     box containing the new one, and the VI clamp: under HJ_CLAMP_MONOTONE
+ *     the solve's limit depends on its start, so such a request always
+ *     solves cold.  Otherwise the request solves cold.
  *   - Memory: results stay on the device until hj_server_release.  Released
  *     results that are still a key's resident prior are evicted (least
  *     recently used first) when the budget is needed.

@@ -382,18 +382,9 @@ static float bits_to_float(unsigned b) {
 // per window carries the residual and the three list lengths.
 hj_status solve_local(hj_grid g, const hj_solve_opts& o, double dt, hj_solve_stats& stats,
                       std::chrono::steady_clock::time_point t0) {
-  if (g->tile_rows <= 0) {
-    for (int r : tile_candidates(g))
-      if (tile_fits(g, r)) {
-        g->tile_rows = r;
-        break;
-      }
-    if (g->tile_rows <= 0)
-      return fail(HJ_ERR_ARG, "localized stepping needs row tiles, and none fits this grid");
-    drop_graph(g);
-  }
   hjd::DevGrid d = devgrid(g);
-  hjk::LocalLayout L = hjk::local_layout(d);
+  int t = g->tile_rows > 0 ? 256 : g->threads;
+  hjk::LocalLayout L = hjk::local_layout(d, t);
   if (g->local_slabs != L.nslabs || g->local_tiles != L.ntiles) {
     cudaFree(g->slab_resid);
     cudaFree(g->slab_masks);
@@ -428,7 +419,6 @@ hj_status solve_local(hj_grid g, const hj_solve_opts& o, double dt, hj_solve_sta
   int counts[3] = {L.ntiles, L.ntiles, L.ntiles};
   bool first = true;
   double tiles_run = 0.0, tiles_full = 0.0;
-  const int t = g->threads;
   for (;;) {
     long long todo = per;
     if (o.max_steps > 0 && stats.steps + todo > o.max_steps) todo = o.max_steps - stats.steps;
@@ -458,8 +448,8 @@ hj_status solve_local(hj_grid g, const hj_solve_opts& o, double dt, hj_solve_sta
     }
     tiles_run += (double)todo * (counts[0] + counts[1] + counts[2]);
     tiles_full += (double)todo * 3.0 * L.ntiles;
-    HJ_CU(hjk::launch_local_lists(d, o.scheme, g->slab_resid, (float)o.local_tol, kax[0], kax[1],
-                                  g->slab_masks, g->tile_lists, g->tile_counts, s));
+    HJ_CU(hjk::launch_local_lists(d, o.scheme, t, g->slab_resid, (float)o.local_tol, kax[0],
+                                  kax[1], g->slab_masks, g->tile_lists, g->tile_counts, s));
     HJ_CU(cudaMemcpyAsync(g->hscal + 4, g->dscal + 4, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     HJ_CU(cudaMemcpyAsync(g->tile_counts_h, g->tile_counts, 3 * sizeof(int),
                           cudaMemcpyDeviceToHost, s));

@@ -321,11 +321,10 @@ hj_status Runner::rebuild() {
   return HJ_OK;
 }
 
-// The group launch of the current membership: every active grid in row
-// tiles of a common block size (the smallest of 256/512/1024 threads that
-// holds a whole line of every grid), each grid with as many lines per tile
-// as fit, and one specialised body per distinct (kind, shape, constants).
-// Group mode is on once the composition's kernels are compiled and loaded.
+// The group launch of the current membership: every active grid in blocks
+// of kGroupThreads nodes of its flat mapping, one specialised body per
+// distinct (kind, shape, constants).  Group mode is on once the
+// composition's kernels are compiled and loaded.
 bool Runner::plan_group() {
   // a loaded kernel serves any membership whose codes it holds (grids that
   // retire from a batch leave a subset)
@@ -333,7 +332,6 @@ bool Runner::plan_group() {
   std::vector<std::string> keep_keys = keep_handle ? gkeys_ : std::vector<std::string>();
   std::vector<hjd::DevGrid> keep_codes = gcodes_;
   std::vector<int> keep_schemes = gschemes_;
-  int keep_T = gthreads_, keep_smem = gsmem_;
   group_mode_ = false;
   group_pending_ = false;
   group_handle_ = nullptr;
@@ -341,11 +339,7 @@ bool Runner::plan_group() {
   gschemes_.clear();
   gkeys_.clear();
   if (!group_allowed_ || nitems_ < 1 || nitems_ > kGroupItems) return false;
-  int maxn = 0;
-  for (int k : order_) maxn = std::max(maxn, slots_[k].g->n[slots_[k].g->ndim - 1]);
-  if (maxn > hjk::kTileMaxThreads) return false;
-  int T = maxn <= 256 ? 256 : (maxn <= 512 ? 512 : 1024);
-  bool reuse = keep_handle && T == keep_T;
+  bool reuse = keep_handle != nullptr;
   if (reuse) {
     gkeys_ = keep_keys;
     gcodes_ = keep_codes;
@@ -354,16 +348,12 @@ bool Runner::plan_group() {
   std::memset(&gpack_, 0, sizeof(gpack_));
   std::vector<std::string>& keys = gkeys_;
   unsigned blocks = 0;
-  int smem = 0;
   for (int i = 0; i < nitems_; ++i) {
     int k = order_[i];
     const Slot& s = slots_[k];
     hj_grid g = s.g;
     hjd::DevGrid d = hja::devgrid(g);
-    int n = d.n[d.ndim - 1];
-    d.tile_rows = std::max(1, std::min(T / n, d.nrows));
-    const void* f[3] = {g->W, g->A, g->B};
-    if (!hjk::tile_ok(d, d.tile_rows, f, 3)) return false;
+    d.tile_rows = 0;
     std::string key = hjk::code_key(d, s.scheme);
     int code = -1;
     for (size_t c = 0; c < keys.size(); ++c)
@@ -375,8 +365,6 @@ bool Runner::plan_group() {
       gcodes_.push_back(d);
       gschemes_.push_back(s.scheme);
     }
-    int radius = s.scheme == 5 ? 3 : (s.scheme == 2 ? 2 : 1);
-    smem = std::max(smem, d.tile_rows * (n + 2 * radius));
     GroupItem& it = gpack_.items[i];
     it.g = d;
     float dt = (float)s.dt;
@@ -385,21 +373,19 @@ bool Runner::plan_group() {
     it.a[2] = hjd::StageArgs{g->B, g->W, g->W, g->snap, nullptr, dt, 0, s.clamp, s.band, s.margin};
     it.slot = k;
     it.code = code;
+    it.bx = (d.plane + kGroupThreads - 1) / kGroupThreads;
     gpack_.block_begin[i] = (int)blocks;
-    blocks += (unsigned)((d.nrows + d.tile_rows - 1) / d.tile_rows);
+    blocks += (unsigned)it.bx * (unsigned)(d.ndim == 4 ? d.n[0] : 1);
   }
   gpack_.count = nitems_;
   gpack_.block_begin[nitems_] = (int)blocks;
   gblocks_ = blocks;
-  gthreads_ = T;
-  if (reuse && smem <= keep_smem) {
-    gsmem_ = keep_smem;
+  if (reuse) {
     group_handle_ = keep_handle;
     group_mode_ = true;
     return true;
   }
-  gsmem_ = smem;
-  group_mode_ = hjk::group_prepare(gcodes_, gschemes_, gthreads_, gsmem_, &group_handle_);
+  group_mode_ = hjk::group_prepare(gcodes_, gschemes_, kGroupThreads, &group_handle_);
   group_pending_ = !group_mode_ && hjk::jit_enabled();
   return group_mode_;
 }
@@ -414,7 +400,7 @@ cudaError_t Runner::enqueue_round(long long R, cudaStream_t s) {
     for (long long i = 0; i < R; ++i) {
       for (int stage = 1; stage <= 3; ++stage) {
         cudaError_t e = hjk::group_launch(group_handle_, stage, &gpack_, dev_ctl_, gblocks_,
-                                          gthreads_, s);
+                                          kGroupThreads, s);
         if (e != cudaSuccess) return e;
       }
       batch_control<<<1, 256, 0, s>>>(dev_slots_, nitems_, dev_ctl_);
@@ -465,7 +451,7 @@ hj_status Runner::round(bool use_graph) {
   hj_status st;
   // the group kernels of the current membership finished compiling: switch
   if (!dirty_ && group_pending_ && !group_mode_) {
-    group_mode_ = hjk::group_prepare(gcodes_, gschemes_, gthreads_, gsmem_, &group_handle_);
+    group_mode_ = hjk::group_prepare(gcodes_, gschemes_, kGroupThreads, &group_handle_);
     if (group_mode_) {
       group_pending_ = false;
       drop_graphs();

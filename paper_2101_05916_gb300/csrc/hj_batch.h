@@ -102,7 +102,7 @@ class Runner {
   std::vector<int> order_;  // slots in the current item list
   std::map<std::string, cudaGraphExec_t> graphs_;  // round shape -> graph
   cudaStream_t cap_stream_ = nullptr;
-  // Group mode: one launch per RK stage over the row tiles of every active
+  // Group mode: one launch per RK stage over the blocks of every active
   // grid, with the kernels compiled for this composition (hj_group.cuh).
   // Until they are compiled the per-kind launches above run.
   bool group_allowed_ = false;
@@ -111,7 +111,6 @@ class Runner {
   void* group_handle_ = nullptr;
   GroupPack gpack_;
   unsigned gblocks_ = 0;
-  int gthreads_ = 0, gsmem_ = 0;
   std::vector<hjd::DevGrid> gcodes_;
   std::vector<int> gschemes_;
   std::vector<std::string> gkeys_;  // code keys of the kernels in group_handle_

@@ -20,17 +20,20 @@ struct Ctl {
   float last_resid;
 };
 
-// One grid of a group launch.  Its tiles are g.tile_rows lines of its
-// fastest axis each; `code` selects the body of the group kernel compiled
-// for its kind, shape and model constants.
+// One grid of a group launch: bx blocks of kGroupThreads nodes per slab of
+// the flat mapping (by slabs: the first axis of a 4-D grid, else one);
+// `code` selects the body of the group kernel compiled for its kind, shape
+// and model constants.
 struct GroupItem {
   hjd::DevGrid g;
   hjd::StageArgs a[3];  // stage 1..3 arguments (check and resid are set on the device)
   int slot;             // index into the control array
   int code;
+  int bx;
 };
 
 constexpr int kGroupItems = 16;
+constexpr int kGroupThreads = 256;
 struct GroupPack {
   int count;
   int block_begin[kGroupItems + 1];
@@ -38,12 +41,12 @@ struct GroupPack {
 };
 
 // The block's item of a group launch: its index (binary search over the
-// block offsets), its tile, and its stage arguments with the window check
-// of stage 3 decided from the control state.  -1 when the grid no longer
-// steps (the whole block returns).
+// block offsets), its block (bx, yb) in the item's flat mapping, and its
+// stage arguments with the window check of stage 3 decided from the control
+// state.  -1 when the grid no longer steps (the whole block returns).
 template <int STAGE>
 __device__ __forceinline__ int group_find(const GroupPack& pack, Ctl* ctl, hjd::StageArgs& a,
-                                          int& tile, bool& check) {
+                                          int& bx, int& yb, bool& check) {
   int lo = 0, hi = pack.count - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
@@ -53,7 +56,9 @@ __device__ __forceinline__ int group_find(const GroupPack& pack, Ctl* ctl, hjd::
   const GroupItem& it = pack.items[lo];
   const Ctl& c = ctl[it.slot];
   if (!c.active) return -1;
-  tile = (int)blockIdx.x - pack.block_begin[lo];
+  int lb = (int)blockIdx.x - pack.block_begin[lo];
+  yb = lb / it.bx;
+  bx = lb - yb * it.bx;
   a = it.a[STAGE - 1];
   check = false;
   if (STAGE == 3) {

@@ -33,19 +33,22 @@ TileShape tile_shape(const hjd::DevGrid& g, int scheme);
 bool tile_ok(const hjd::DevGrid& g, int tile_rows, const void* const* fields, int nfields);
 
 // Localized stepping over slabs (hjd::slab_of): the slab lattice is
-// s0 x s1, and every slab holds rows_per_slab consecutive fastest-axis lines.
+// s0 x s1, and every slab is a run of nodes_per_slab consecutive nodes.
+// Tiles are the blocks of the stage launch: row tiles (g.tile_rows > 0), or
+// blocks of `threads` nodes of the flat mapping, `per` of them per slab of
+// the flat mapping's grid.
 struct LocalLayout {
-  int s0 = 1, s1 = 1, nslabs = 1, rows_per_slab = 1, ntiles = 0;
+  int s0 = 1, s1 = 1, nslabs = 1, nodes_per_slab = 1, ntiles = 0, per = 0, threads = 0;
 };
-LocalLayout local_layout(const hjd::DevGrid& g);
+LocalLayout local_layout(const hjd::DevGrid& g, int threads);
 // From the window's per-slab changes (float bits, nslabs entries): the slab
 // masks (3 x nslabs bytes: live, ring2, ring1) and the row-tile lists of the
 // three stages (3 x ntiles ints) with their lengths in counts[0..2].  A
 // slab steps when one that changed by more than thr lies within k0 slabs
 // along the first slab axis and k1 along the second.
-cudaError_t launch_local_lists(const hjd::DevGrid& g, int scheme, const unsigned* slab_resid,
-                               float thr, int k0, int k1, unsigned char* masks, int* lists,
-                               int* counts, cudaStream_t s);
+cudaError_t launch_local_lists(const hjd::DevGrid& g, int scheme, int threads,
+                               const unsigned* slab_resid, float thr, int k0, int k1,
+                               unsigned char* masks, int* lists, int* counts, cudaStream_t s);
 
 // Streaming multiprocessors of the current device (read once per device).
 int num_sms();
@@ -71,12 +74,12 @@ bool jit_prepare(const hjd::DevGrid& g, int scheme, int threads);
 cudaError_t jit_launch(const hjd::DevGrid& g, int scheme, int stage, const hjd::StageArgs& a,
                        cudaStream_t s, int threads, bool* used);
 // Group kernels of a batch (hj_group.cuh): codes[c] is a representative
-// grid descriptor (row tiles set) of code c, run with schemes[c]; threads per
-// block and shared floats per block are common to all codes.  The first
-// sight of a composition starts its background compile; true (and *handle)
-// once it is loaded.  Must not be called inside a stream capture.
+// grid descriptor of code c, run with schemes[c]; threads per block are
+// common to all codes.  The first sight of a composition starts its
+// background compile; true (and *handle) once it is loaded.  Must not be
+// called inside a stream capture.
 bool group_prepare(const std::vector<hjd::DevGrid>& codes, const std::vector<int>& schemes,
-                   int threads, int smem_floats, void** handle);
+                   int threads, void** handle);
 // One group launch of stage 1..3 over `blocks` blocks; pack points at a
 // hjb::GroupPack, ctl is the device control array.
 cudaError_t group_launch(void* handle, int stage, const void* pack, void* ctl, unsigned blocks,

@@ -212,24 +212,20 @@ std::string source(const hjd::DevGrid& g, int scheme, int threads) {
                   "hj_stage_%d(const hjd::DevGrid g, const hjd::StageArgs a) {\n",
                   threads, st);
     s += buf;
-    std::snprintf(buf, sizeof(buf),
-                  "  unsigned r = hjd::stage_point<%d, %d, %d, %d>(hj_fixed(g), a,\n"
-                  "      blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y, a.check != 0);\n",
+    std::snprintf(buf, sizeof(buf), "  hjd::flat_body<%d, %d, %d, %d>(hj_fixed(g), a);\n}\n",
                   g.ndim, scheme, g.model, st);
     s += buf;
-    if (st == 3) s += "  if (a.check) hjd::block_max_bits(r, a.resid);\n";
-    else s += "  (void)r;\n";
-    s += "}\n";
   }
   return s;
 }
 
-// The group kernels of a batch: one kernel per RK stage over the row tiles
-// of every grid in a hjb::GroupPack.  Each distinct (kind, shape, model
-// constants) is one `code` with its own specialised body; a block finds its
-// grid, returns if that grid no longer steps, and runs the body of its code.
+// The group kernels of a batch: one kernel per RK stage over the blocks of
+// every grid in a hjb::GroupPack (the flat mapping, `threads` per block).
+// Each distinct (kind, shape, model constants) is one `code` with its own
+// specialised body; a block finds its grid, returns if that grid no longer
+// steps, and runs the body of its code.
 std::string group_source(const std::vector<hjd::DevGrid>& codes, const std::vector<int>& schemes,
-                         int threads, int smem_floats) {
+                         int threads) {
   std::string s = "#include \"hj_group.cuh\"\n";
   for (size_t c = 0; c < codes.size(); ++c) s += fixed_fn("hj_fixed_" + std::to_string(c), codes[c]);
   char buf[512];
@@ -237,24 +233,22 @@ std::string group_source(const std::vector<hjd::DevGrid>& codes, const std::vect
     std::snprintf(buf, sizeof(buf),
                   "extern \"C\" __global__ void __launch_bounds__(%d)\n"
                   "hj_group_%d(const __grid_constant__ hjb::GroupPack pack, hjb::Ctl* ctl) {\n"
-                  "  __shared__ float sm[%d];\n"
-                  "  hjd::StageArgs a;\n  int tile;\n  bool check;\n"
-                  "  int k = hjb::group_find<%d>(pack, ctl, a, tile, check);\n"
-                  "  if (k < 0) return;\n"
+                  "  hjd::StageArgs a;\n  int bx, yb;\n  bool check;\n"
+                  "  int k = hjb::group_find<%d>(pack, ctl, a, bx, yb, check);\n"
+                  "  if (k < 0) return;\n  unsigned r = 0u;\n"
+                  "  const int q = bx * %d + (int)threadIdx.x;\n"
                   "  switch (pack.items[k].code) {\n",
-                  threads, st, smem_floats, st);
+                  threads, st, st, threads);
     s += buf;
     for (size_t c = 0; c < codes.size(); ++c) {
       std::snprintf(buf, sizeof(buf),
-                    "    case %d: {\n"
-                    "      hjd::TileOut o = hjd::stage_tile<%d, %d, %d, %d>(hj_fixed_%d(pack.items[k].g),"
-                    " a, tile, check, sm);\n"
-                    "      %s\n      break;\n    }\n",
-                    (int)c, codes[c].ndim, schemes[c], codes[c].model, st, (int)c,
-                    st == 3 ? "if (check) hjd::block_max_bits(o.resid, a.resid);" : "(void)o;");
+                    "    case %d: r = hjd::stage_point<%d, %d, %d, %d>(hj_fixed_%d(pack.items[k].g),"
+                    " a, q, yb, check); break;\n",
+                    (int)c, codes[c].ndim, schemes[c], codes[c].model, st, (int)c);
       s += buf;
     }
-    s += "  }\n}\n";
+    s += "  }\n";
+    s += st == 3 ? "  if (check) hjd::block_max_bits(r, a.resid);\n}\n" : "  (void)r;\n}\n";
   }
   return s;
 }
@@ -392,10 +386,10 @@ std::map<std::string, std::shared_ptr<Entry>> g_group_cache;
 }  // namespace
 
 bool group_prepare(const std::vector<hjd::DevGrid>& codes, const std::vector<int>& schemes,
-                   int threads, int smem_floats, void** handle) {
+                   int threads, void** handle) {
   *handle = nullptr;
   if (!enabled() || codes.empty()) return false;
-  std::string key = std::to_string(threads) + "/" + std::to_string(smem_floats);
+  std::string key = std::to_string(threads) + "/";
   for (size_t c = 0; c < codes.size(); ++c) {
     Key k = key_of(codes[c], schemes[c], threads);
     key.append(reinterpret_cast<const char*>(&k), sizeof(k));
@@ -411,7 +405,7 @@ bool group_prepare(const std::vector<hjd::DevGrid>& codes, const std::vector<int
         e->state.store(3);
         return false;
       }
-      compile_async(e, group_source(codes, schemes, threads, smem_floats));
+      compile_async(e, group_source(codes, schemes, threads));
       return false;
     }
     e = it->second;
@@ -466,6 +460,9 @@ cudaError_t jit_launch(const hjd::DevGrid& g, int scheme, int stage, const hjd::
     TileShape ts = tile_shape(g, scheme);
     grid = dim3(a.tiles ? (unsigned)a.ntiles : ts.blocks, 1, 1);
     block = dim3(ts.threads, 1, 1);
+  } else if (a.tiles) {
+    grid = dim3((unsigned)a.ntiles, 1, 1);
+    block = dim3(threads, 1, 1);
   } else {
     grid = dim3((unsigned)((g.plane + threads - 1) / threads), g.ndim == 4 ? (unsigned)g.n[0] : 1u,
                 1);
@@ -547,11 +544,6 @@ extern "C" hj_status hj_jit_check_group(int ngrids, const int* ndims, const int*
     return hja::fail(HJ_ERR_ARG, "bad group description");
   std::vector<hjd::DevGrid> codes;
   std::vector<int> sch;
-  int maxn = 0;
-  for (int k = 0; k < ngrids; ++k) maxn = std::max(maxn, shapes[4 * k + ndims[k] - 1]);
-  if (maxn > hjk::kTileMaxThreads) return hja::fail(HJ_ERR_ARG, "a line is longer than a tile");
-  int T = maxn <= 256 ? 256 : (maxn <= 512 ? 512 : 1024);
-  int smem = 0;
   for (int k = 0; k < ngrids; ++k) {
     int nd = ndims[k];
     if (nd < 1 || nd > HJ_MAX_DIM) return hja::fail(HJ_ERR_ARG, "bad ndim");
@@ -569,22 +561,19 @@ extern "C" hj_status hj_jit_check_group(int ngrids, const int* ndims, const int*
       g.cb[i] = 0.75;
       npts *= n;
     }
+    if (npts >= (1ll << 31)) return hja::fail(HJ_ERR_ARG, "grid too large");
     g.npts = npts;
     g.model = models[k];
     g.con_kind = hjd::C_BOX;
     if (!hjk::stage_supported(models[k], nd, schemes[k]))
       return hja::fail(HJ_ERR_ARG, "model %d, %d-D, scheme %d has no stencil", models[k], nd,
                        schemes[k]);
-    hjd::DevGrid d = hja::devgrid(&g);
-    int n = d.n[nd - 1];
-    d.tile_rows = std::max(1, std::min(T / n, d.nrows));
-    smem = std::max(smem, d.tile_rows * (n + 2 * hjk::radius_of(schemes[k])));
-    codes.push_back(d);
+    codes.push_back(hja::devgrid(&g));
     sch.push_back(schemes[k]);
   }
   if (!hjk::nvrtc().ok) return hja::fail(HJ_ERR_CUDA, "NVRTC could not be loaded");
   std::string log;
-  std::vector<char> cubin = hjk::compile(hjk::group_source(codes, sch, T, smem), &log);
+  std::vector<char> cubin = hjk::compile(hjk::group_source(codes, sch, hjb::kGroupThreads), &log);
   if (cubin.empty()) return hja::fail(HJ_ERR_CUDA, "NVRTC: %.400s", log.c_str());
   return HJ_OK;
 }

@@ -33,11 +33,7 @@ using hjd::StageArgs;
 
 template <int D, int S, int M, int STAGE, int THREADS>
 __global__ void __launch_bounds__(THREADS) stage_kernel(const DevGrid g, const StageArgs a) {
-  unsigned r = hjd::stage_point<D, S, M, STAGE>(g, a, blockIdx.x * blockDim.x + threadIdx.x,
-                                                blockIdx.y, a.check != 0);
-  if constexpr (STAGE == 3) {
-    if (a.check) hjd::block_max_bits(r, a.resid);
-  }
+  hjd::flat_body<D, S, M, STAGE>(g, a);
 }
 
 // Row-tile variant: block b stages lines [b R, b R + R) of the fastest axis
@@ -192,7 +188,7 @@ static dim3 stage_grid(const DevGrid& g, int threads) {
 
 template <int D, int S, int M, int T>
 static void stage_launch(const DevGrid& g, int stage, const StageArgs& a, cudaStream_t s) {
-  dim3 grid = stage_grid(g, T), block(T);
+  dim3 grid = a.tiles ? dim3((unsigned)a.ntiles, 1u, 1u) : stage_grid(g, T), block(T);
   switch (stage) {
     case 1: stage_kernel<D, S, M, 1, T><<<grid, block, 0, s>>>(g, a); break;
     case 2: stage_kernel<D, S, M, 2, T><<<grid, block, 0, s>>>(g, a); break;
@@ -275,7 +271,6 @@ cudaError_t launch_stage(const DevGrid& g, int scheme, int stage, const StageArg
                          int threads, bool allow_jit) {
   if (threads != 128 && threads != 512) threads = 256;
   if (g.tile_rows > 0 && (reinterpret_cast<uintptr_t>(a.src) & 15u)) return cudaErrorInvalidValue;
-  if (g.tile_rows <= 0 && (a.tiles || a.live || a.slab_resid)) return cudaErrorInvalidValue;
   if (a.tiles && a.ntiles == 0) return cudaSuccess;
   if (allow_jit) {
     bool used = false;
@@ -405,18 +400,31 @@ __global__ void local_masks_kernel(const unsigned* __restrict__ resid, int s0, i
 }
 
 // Tile lists of the next window: list q (q = 0, 1, 2 for stages 1, 2, 3)
-// gets every row tile that holds a line of a slab in mask q (ring1, ring2,
-// live).  counts[q] must be zero on entry.  The order within a list does not
-// matter: tiles are independent within a stage.
-__global__ void local_lists_kernel(int ntiles, int tile_rows, int nrows, int rows_per_slab,
+// gets every tile that holds a node of a slab in mask q (ring1, ring2,
+// live).  Tile t covers the nodes [first(t), last(t)] of the flat node
+// order: row tiles hold tile_rows lines of n_last nodes; flat tiles are the
+// blocks of `threads` nodes of the flat mapping, `per` blocks per slab of
+// `plane` nodes.  Slabs are runs of nodes_per_slab nodes.  counts[q] must be
+// zero on entry; the order within a list does not matter.
+__global__ void local_lists_kernel(int ntiles, int tile_rows, int n_last, int threads, int per,
+                                   int plane, int npts, int nodes_per_slab,
                                    const unsigned char* __restrict__ ring1,
                                    const unsigned char* __restrict__ ring2,
                                    const unsigned char* __restrict__ live, int* lists,
                                    int* counts) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ntiles) return;
-  int r0 = t * tile_rows, r1 = min(r0 + tile_rows, nrows) - 1;
-  int f = r0 / rows_per_slab, l = r1 / rows_per_slab;
+  long long first, last;
+  if (tile_rows > 0) {
+    first = (long long)t * tile_rows * n_last;
+    last = min(first + (long long)tile_rows * n_last, (long long)npts) - 1;
+  } else {
+    int yb = t / per, bx = t - yb * per;
+    long long q0 = (long long)bx * threads;
+    first = (long long)yb * plane + q0;
+    last = (long long)yb * plane + min(q0 + threads, (long long)plane) - 1;
+  }
+  int f = (int)(first / nodes_per_slab), l = (int)(last / nodes_per_slab);
   bool m1 = false, m2 = false, m3 = false;
   for (int sl = f; sl <= l; ++sl) {
     m1 = m1 || ring1[sl];
@@ -428,30 +436,31 @@ __global__ void local_lists_kernel(int ntiles, int tile_rows, int nrows, int row
   if (m3) lists[2 * ntiles + atomicAdd(counts + 2, 1)] = t;
 }
 
-LocalLayout local_layout(const DevGrid& g) {
+LocalLayout local_layout(const DevGrid& g, int threads) {
   LocalLayout L;
   if (g.ndim == 4) {
     L.s0 = g.n[0];
     L.s1 = g.n[1];
-    L.rows_per_slab = g.n[2];
   } else if (g.ndim >= 2) {
     L.s0 = g.n[0];
     L.s1 = 1;
-    L.rows_per_slab = g.ndim == 3 ? g.n[1] : 1;
-  } else {
-    L.s0 = 1;
-    L.s1 = 1;
-    L.rows_per_slab = 1;
   }
   L.nslabs = L.s0 * L.s1;
-  L.ntiles = g.tile_rows > 0 ? (g.nrows + g.tile_rows - 1) / g.tile_rows : 0;
+  L.nodes_per_slab = g.npts / L.nslabs;
+  L.threads = threads;
+  if (g.tile_rows > 0) {
+    L.ntiles = (g.nrows + g.tile_rows - 1) / g.tile_rows;
+  } else {
+    L.per = (g.plane + threads - 1) / threads;
+    L.ntiles = L.per * (g.ndim == 4 ? g.n[0] : 1);
+  }
   return L;
 }
 
-cudaError_t launch_local_lists(const DevGrid& g, int scheme, const unsigned* slab_resid,
-                               float thr, int k0, int k1, unsigned char* masks, int* lists,
-                               int* counts, cudaStream_t s) {
-  LocalLayout L = local_layout(g);
+cudaError_t launch_local_lists(const DevGrid& g, int scheme, int threads,
+                               const unsigned* slab_resid, float thr, int k0, int k1,
+                               unsigned char* masks, int* lists, int* counts, cudaStream_t s) {
+  LocalLayout L = local_layout(g, threads);
   int radius = scheme == 5 ? 3 : (scheme == 2 ? 2 : 1);
   unsigned char *live = masks, *ring2 = masks + L.nslabs, *ring1 = masks + 2 * L.nslabs;
   cudaError_t e = cudaMemsetAsync(counts, 0, 3 * sizeof(int), s);
@@ -459,9 +468,9 @@ cudaError_t launch_local_lists(const DevGrid& g, int scheme, const unsigned* sla
   local_masks_kernel<<<(L.nslabs + 255) / 256, 256, 0, s>>>(slab_resid, L.s0, L.s1, thr, k0,
                                                            L.s1 > 1 ? k1 : 0, radius, live,
                                                            ring2, ring1);
-  local_lists_kernel<<<(L.ntiles + 255) / 256, 256, 0, s>>>(L.ntiles, g.tile_rows, g.nrows,
-                                                           L.rows_per_slab, ring1, ring2, live,
-                                                           lists, counts);
+  local_lists_kernel<<<(L.ntiles + 255) / 256, 256, 0, s>>>(
+      L.ntiles, g.tile_rows, g.n[g.ndim - 1], threads, L.per, g.plane, g.npts, L.nodes_per_slab,
+      ring1, ring2, live, lists, counts);
   g_launches.fetch_add(2, std::memory_order_relaxed);
   return cudaGetLastError();
 }

@@ -288,7 +288,10 @@ void hj_server_s::admit_locked(std::vector<long long>& admitted) {
       it = queue.erase(it);
       continue;
     }
-    if (s == HJ_OK && q.r.mode == HJ_WARM && q.r.key != 0) {
+    // Only the VI clamp (Eq. 2) reaches the same fixed point from every
+    // dominating start.  Under the monotone clamp the limit depends on the
+    // start, so such a request always solves cold.
+    if (s == HJ_OK && q.r.mode == HJ_WARM && q.r.key != 0 && q.r.opts.clamp == HJ_CLAMP_VI) {
       auto rk = resident_of_key.find(q.r.key);
       if (rk != resident_of_key.end()) {
         Req& p = reqs[rk->second];

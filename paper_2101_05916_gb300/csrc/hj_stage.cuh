@@ -105,6 +105,57 @@ __device__ __forceinline__ unsigned stage_point(const DevGrid& g, const StageArg
   return stage_node<D, S, M, STAGE>(g, a, idx, p, check, nullptr);
 }
 
+// What one thread's node gives back to its block: the stop-test residual
+// bits (band and margin rules applied), the node's change for its slab's
+// residual, and its slab (-1 for a thread without a node).
+struct NodeOut {
+  unsigned resid;
+  unsigned raw;
+  int slab;
+};
+
+// Per-slab maximum of v into out[slab], one atomic per run of lanes that
+// share a slab (slab < 0: no node).  Every lane of the warp must call it.
+__device__ __forceinline__ void slab_max_bits(int slab, unsigned v, unsigned* out) {
+  unsigned m = __match_any_sync(0xffffffffu, slab);
+  unsigned w = __reduce_max_sync(m, v);
+  if (slab >= 0 && w && (int)(threadIdx.x & 31) == __ffs(m) - 1) atomicMax(out + slab, w);
+}
+
+// Blocks of the flat mapping per slab yb.
+__device__ __forceinline__ int flat_blocks_per_slab(const DevGrid& g) {
+  return (g.plane + (int)blockDim.x - 1) / (int)blockDim.x;
+}
+
+// Body of a flat stage kernel.  Without a tile list, block (x, y) covers
+// nodes x * blockDim .. of slab y; with one, block b runs flat tile
+// tiles[b] = y * (blocks per slab) + x.  Stage 3 with check folds the
+// stop-test residual of the block into *a.resid and, in a localized solve,
+// every node's change into its slab's entry of a.slab_resid.
+template <int D, int S, int M, int STAGE>
+__device__ __forceinline__ void flat_body(const DevGrid& g, const StageArgs& a) {
+  int bx = (int)blockIdx.x, yb = (int)blockIdx.y;
+  if (a.tiles) {
+    int t = a.tiles[blockIdx.x];
+    int per = flat_blocks_per_slab(g);
+    yb = t / per;
+    bx = t - yb * per;
+  }
+  NodeOut o{0u, 0u, -1};
+  int idx[D];
+  int p;
+  if (node_of<D>(g, bx * (int)blockDim.x + (int)threadIdx.x, yb, idx, p)) {
+    o.slab = slab_of<D>(g, idx);
+    o.resid = stage_node<D, S, M, STAGE>(g, a, idx, p, a.check != 0, nullptr, &o.raw);
+  }
+  if constexpr (STAGE == 3) {
+    if (a.check) {
+      if (a.slab_resid) slab_max_bits(o.slab, o.raw, a.slab_resid);
+      block_max_bits(o.resid, a.resid);
+    }
+  }
+}
+
 // Shared-memory floats of one row tile: tile_rows rows of n + 2 R values.
 template <int S>
 __host__ __device__ constexpr int tile_row_pitch(int n) {
@@ -197,14 +248,6 @@ __device__ __forceinline__ TileOut stage_tile(const DevGrid& g, const StageArgs&
   out.resid = stage_node<D, S, M, STAGE>(g, a, idx, base + t, check, sm + r * P + R + idx[D - 1],
                                          &out.raw);
   return out;
-}
-
-// Per-slab maximum of v into out[slab], one atomic per run of lanes that
-// share a slab (slab < 0: no node).  Every lane of the warp must call it.
-__device__ __forceinline__ void slab_max_bits(int slab, unsigned v, unsigned* out) {
-  unsigned m = __match_any_sync(0xffffffffu, slab);
-  unsigned w = __reduce_max_sync(m, v);
-  if (slab >= 0 && w && (int)(threadIdx.x & 31) == __ffs(m) - 1) atomicMax(out + slab, w);
 }
 
 // Body of a row-tile stage kernel: the block's tile comes from the tile list

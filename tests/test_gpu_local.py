@@ -65,9 +65,11 @@ def test_localized_update_z_matches_full_and_oracle(hj, scheme):
     assert np.abs(Wl - Wf).max() <= REL * scale
     assert sign_agreement_far(Wl, Wf) >= SIGN_FRAC
     assert loc["stepped"] < 1.0, loc
-    # against the oracle's own warm solve from its own prior
-    Wp, _ = oracle.solve(spec, scheme=scheme, tol=1e-7, dfield=base, max_steps=80000)
-    Wo, sto = oracle.solve(spec, scheme=scheme, tol=1e-7, dfield=raised, warm=Wp,
+    # against the oracle's own warm solve from its own prior; ENO2 stencil
+    # switching near the bump holds the window residual near 1e-6, so the
+    # oracle stops at 1e-5 per window as the GPU does
+    Wp, _ = oracle.solve(spec, scheme=scheme, tol=1e-5, dfield=base, max_steps=80000)
+    Wo, sto = oracle.solve(spec, scheme=scheme, tol=1e-5, dfield=raised, warm=Wp,
                            max_steps=80000)
     assert sto["converged"]
     assert np.abs(Wl - Wo).max() <= REL * np.abs(Wo).max()
@@ -98,10 +100,30 @@ def test_localized_update_x4_matches_full_warm_and_steps_less(hj):
     assert sign_agreement_far(Wl, Wo) >= SIGN_FRAC
 
 
+def test_localized_stepping_on_row_tiles_matches_flat(hj):
+    """Localized stepping runs on either launch shape: row tiles give the
+    flat mapping's result bit for bit."""
+    spec = wl.quad_x4(15, 0.3)
+    base = wl.wind_field(spec, 0.3, 0.0, 0, 0.0, 1.0)
+    raised = wl.wind_field(spec, 0.3, 0.6, 0, 3.5, 0.6)
+    out = []
+    for rows in (0, 7):
+        g = hj.Grid.from_spec(spec)
+        g.set_launch_shape(256, rows)
+        g.set_disturbance_field(*base)
+        g.solve(hj.HJ_COLD, scheme=5, tol=1e-4, clamp=1, band=0.5, max_steps=20000)
+        g.set_disturbance_field(*raised)
+        st = g.solve(hj.HJ_WARM, scheme=5, tol=1e-4, clamp=1, band=0.5, max_steps=20000,
+                     local_tol=1e-6)
+        out.append((g.value(), st["steps"], st["stepped"]))
+        g.close()
+    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+
+
 def test_localized_stepping_edges(hj):
     """Everything quiet: nothing steps after the first window and the solve
-    stops there; fixed-step runs ignore the option; a flat launch shape is
-    switched to row tiles; bad settings are rejected."""
+    stops there; fixed-step runs ignore the option; bad settings are
+    rejected."""
     spec = wl.quad_z(61, 0.5)
     g = hj.Grid.from_spec(spec)
     g.solve(hj.HJ_COLD, scheme=2, tol=1e-6)
@@ -109,7 +131,7 @@ def test_localized_stepping_edges(hj):
     st = g.solve(hj.HJ_WARM, scheme=2, tol=1e-6, local_tol=1e-6)
     assert st["converged"] and st["windows"] == 1
     assert np.abs(g.value() - W0).max() < 1e-6
-    assert g.launch_shape()[1] > 0
+    assert g.launch_shape() == (256, 0)
     st = g.solve(hj.HJ_WARM, scheme=2, fixed_steps=5, local_tol=1e-6)
     assert st["steps"] == 5 and st["stepped"] == 1.0
     with pytest.raises(hj.HJError):

@@ -535,7 +535,7 @@ def test_group_launch_is_one_launch_per_stage_and_bitwise_equal(hj):
         before = hj.hj_kernel_launches()
         rc, statuses, stats = hj.hj_solve_batch([g.handle for g in grids], [0] * 4, opts)
         launches = hj.hj_kernel_launches() - before
-        assert all(st == 0 for st in statuses)
+        assert rc == 0 and all(st == 0 for st in statuses), (rc, statuses, hj.hj_last_error())
         if fixed:
             # 4 inits, then 3 group launches and 1 control launch per step
             assert launches == 4 + 4 * fixed, launches
@@ -617,6 +617,32 @@ def test_config3_prolong_full_size_sampled(hj):
     expect = np.minimum(vo, lo)
     got = Wf[idx[:, 0], idx[:, 1], idx[:, 2], idx[:, 3]]
     assert np.abs(got - expect).max() <= 2e-6 * np.abs(expect).max()
+
+
+def test_config3_fine_grid_fixed_horizon_full_size(hj):
+    """The adaptive update's fine grid at full size (81^4, 43 M nodes): a
+    seeded coarse field on 31^4 is migrated to 81^4 and stepped 20 times
+    (WENO5, monotone clamp, the shape-specialised kernels the bench times)
+    from that start on both sides, at the oracle's dt; every node compared
+    at the parity bar.  Both sides start from the same float32 coarse
+    values."""
+    c, f, _ = wl.config3()
+    Wc = (oracle.margin(c) + wl.seeded_field(c, 31, 0.05)).astype(np.float32)
+    dt = oracle.cfl_dt(f)
+    gc, gf = hj.Grid.from_spec(c), hj.Grid.from_spec(f)
+    gf.solve(hj.HJ_COLD, scheme=5, fixed_steps=1, dt=dt, clamp=1)
+    assert hj.hj_jit_wait(120.0)
+    gc.set_value(Wc)
+    hj.prolong(gc, gf)
+    st = gf.solve(hj.HJ_WARM, scheme=5, dt=dt, fixed_steps=20, clamp=1)
+    Wg = gf.value()
+    gc.close()
+    gf.close()
+    assert st["steps"] == 20
+    W0 = oracle.prolong(c, Wc.astype(np.float64), f)
+    Wo, _ = oracle.solve(f, scheme=5, dt=dt, fixed_steps=20, clamp=1, warm=W0)
+    del W0
+    assert_parity(Wg, Wo, f)
 
 
 def read_x41_reference():

@@ -243,6 +243,27 @@ def test_coarse_initialisation_in_the_server(hj):
             hj.hj_server_destroy(s2)
 
 
+def test_monotone_clamp_requests_never_warm_start(hj):
+    """Under the monotone clamp a solve's limit depends on its start, so a
+    request with it solves cold even when the key's prior dominates; its
+    result is its own cold solve."""
+    s = hj.hj_server_create(4 << 30, 8)
+    key = 55
+    for b in (0.2, 0.5):
+        spec = wl.quad_z(61, b)
+        rc, st, W = fetch(hj, s, run(hj, s, spec, 2, 0.0, hj.HJ_WARM, key, clamp=1, tol=1e-5),
+                          spec)
+        assert rc == hj.HJ_OK
+    stats = hj.hj_server_get_stats(s)
+    hj.hj_server_destroy(s)
+    assert stats["warm_starts"] == 0 and stats["cold_starts"] == 2
+    g = hj.Grid.from_spec(spec)
+    g.solve(hj.HJ_COLD, scheme=2, tol=1e-5, clamp=1, max_steps=20000)
+    Wc = g.value()
+    g.close()
+    assert np.abs(W - Wc).max() <= REL * np.abs(Wc).max()
+
+
 def test_translated_prior_warm_start(hj):
     """A key's resident prior whose constraint box, moved along the position
     axis, equals the new one warm-starts the request through hj_translate and

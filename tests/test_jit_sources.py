@@ -62,6 +62,8 @@ def test_group_kernel_source_compiles(grids):
 
 def test_group_kernel_bad_arguments_are_rejected():
     with pytest.raises(hj.HJError):
-        hj.hj_jit_check_group([((5, 2000), "drift", 2)])  # a line longer than any tile
-    with pytest.raises(hj.HJError):
         hj.hj_jit_check_group([((41, 41), "quad_x4", 5)])  # no such stencil
+    with pytest.raises(hj.HJError):
+        hj.hj_jit_check_group([((41, 2), "drift", 2)])  # an axis with fewer than 3 nodes
+    with pytest.raises(hj.HJError):
+        hj.hj_jit_check_group([((41, 41), "quad_z", 3)])  # no such scheme
