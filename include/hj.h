@@ -111,9 +111,9 @@ typedef struct {
                          /* only slabs whose value changed by more than local_tol in the  */
                          /* last window (nodes within band_margin of a free face do not   */
                          /* count; nodes outside the band do), and slabs close enough to  */
-                         /* them for a change to arrive within the next window (the CFL   */
-                         /* distance of a window along each slab axis, plus               */
-                         /* local_margin slabs), step;                                    */
+                         /* them for a change to arrive before the masks are refreshed    */
+                         /* (four times a window; the CFL distance of a quarter window    */
+                         /* along each slab axis, plus local_margin slabs), step;         */
                          /* the others keep their value.  Slabs are the lines of the two  */
                          /* slowest axes of a 4-D grid, the first axis of a 2-D or 3-D    */
                          /* grid.  Stage values next to stepping slabs are recomputed on  */

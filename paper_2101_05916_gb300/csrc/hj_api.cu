@@ -376,8 +376,11 @@ static float bits_to_float(unsigned b) {
 //     and the rings on which stages 1 and 2 are recomputed (2 and 1
 //     stencil radii further), and a list kernel turns them into the row
 //     tiles of each stage;
-//   - the next window launches exactly those tiles; stage 3 commits only
-//     stepping slabs, the others keep W and their snapshot.
+//   - the next steps launch exactly those tiles; stage 3 commits only
+//     stepping slabs, the others keep W and their snapshot;
+//   - the masks are also refreshed three times inside each window, from the
+//     change since the window began, so that the distance a change can
+//     travel before the next refresh (and with it the margins) stays small.
 // The stop test is the usual one over the nodes that step.  One read-back
 // per window carries the residual and the three list lengths.
 hj_status solve_local(hj_grid g, const hj_solve_opts& o, double dt, hj_solve_stats& stats,
@@ -405,15 +408,17 @@ hj_status solve_local(hj_grid g, const hj_solve_opts& o, double dt, hj_solve_sta
   const float fdt = (float)dt;
   long long per = (long long)std::ceil(o.check_dt / dt - 1e-9);
   if (per < 1) per = 1;
-  // how far (in slabs) a change can travel along each slab axis in one
-  // window: the CFL speed alpha_a dt / h_a cells per step times the steps,
-  // plus the caller's margin
+  // the masks are refreshed every `sub` steps (four times a window); how
+  // far (in slabs) a change can travel along each slab axis in that time:
+  // the CFL speed alpha_a dt / h_a cells per step times the steps, plus the
+  // caller's margin
+  long long sub = std::max(1ll, (per + 3) / 4);
   int kax[2] = {0, 0};
   for (int q = 0; q < 2; ++q) {
     int ax = q;  // slab axes: 0 and 1 of a 4-D grid, 0 of a 2-D or 3-D grid
     int slab_axes = g->ndim == 4 ? 2 : (g->ndim >= 2 ? 1 : 0);
     if (ax >= slab_axes) continue;
-    double cells = (double)per * (double)g->alpha[ax] * dt / g->h[ax];
+    double cells = (double)sub * (double)g->alpha[ax] * dt / g->h[ax];
     kax[q] = (int)std::ceil(cells) + 1 + o.local_margin;
   }
   int counts[3] = {L.ntiles, L.ntiles, L.ntiles};
@@ -443,11 +448,29 @@ hj_status solve_local(hj_grid g, const hj_solve_opts& o, double dt, hj_solve_sta
     for (long long i = 0; i < todo; ++i) {
       HJ_CU(hjk::launch_stage(d, o.scheme, 1, a1, s, t));
       HJ_CU(hjk::launch_stage(d, o.scheme, 2, a2, s, t));
-      a3.check = (i == todo - 1) ? 1 : 0;
+      bool refresh = (i + 1) % sub == 0 && i != todo - 1;
+      a3.check = (i == todo - 1) ? 1 : (refresh ? 2 : 0);
       HJ_CU(hjk::launch_stage(d, o.scheme, 3, a3, s, t));
+      tiles_run += (double)(counts[0] + counts[1] + counts[2]);
+      tiles_full += 3.0 * L.ntiles;
+      if (refresh) {
+        // mid-window refresh of the masks from the change since the window
+        // began; the rest of the window launches the lists that follow
+        HJ_CU(hjk::launch_local_lists(d, o.scheme, t, g->slab_resid, (float)o.local_tol, kax[0],
+                                      kax[1], g->slab_masks, g->tile_lists, g->tile_counts, s));
+        HJ_CU(cudaMemcpyAsync(g->tile_counts_h, g->tile_counts, 3 * sizeof(int),
+                              cudaMemcpyDeviceToHost, s));
+        HJ_CU(cudaStreamSynchronize(s));
+        for (int q = 0; q < 3; ++q) counts[q] = g->tile_counts_h[q];
+        a1.tiles = g->tile_lists;
+        a2.tiles = g->tile_lists + L.ntiles;
+        a3.tiles = g->tile_lists + 2 * L.ntiles;
+        a1.ntiles = counts[0];
+        a2.ntiles = counts[1];
+        a3.ntiles = counts[2];
+        a3.live = g->slab_masks;
+      }
     }
-    tiles_run += (double)todo * (counts[0] + counts[1] + counts[2]);
-    tiles_full += (double)todo * 3.0 * L.ntiles;
     HJ_CU(hjk::launch_local_lists(d, o.scheme, t, g->slab_resid, (float)o.local_tol, kax[0],
                                   kax[1], g->slab_masks, g->tile_lists, g->tile_counts, s));
     HJ_CU(cudaMemcpyAsync(g->hscal + 4, g->dscal + 4, sizeof(unsigned), cudaMemcpyDeviceToHost, s));

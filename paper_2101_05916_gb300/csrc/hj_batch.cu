@@ -322,69 +322,77 @@ hj_status Runner::rebuild() {
 }
 
 // The group launch of the current membership: every active grid in blocks
-// of kGroupThreads nodes of its flat mapping, one specialised body per
-// distinct (kind, shape, constants).  Group mode is on once the
-// composition's kernels are compiled and loaded.
+// of kGroupThreads nodes of its flat mapping, at a position of the group
+// kernel compiled for a grid of its kind, shape and model constants.  A
+// loaded kernel keeps serving while grids retire from the batch: each grid
+// keeps a position of its own code, and positions left without a grid get
+// no blocks.  Otherwise the current membership's kernel is compiled in the
+// background, and group mode starts once it is loaded.
 bool Runner::plan_group() {
-  // a loaded kernel serves any membership whose codes it holds (grids that
-  // retire from a batch leave a subset)
-  void* keep_handle = group_mode_ ? group_handle_ : nullptr;
-  std::vector<std::string> keep_keys = keep_handle ? gkeys_ : std::vector<std::string>();
-  std::vector<hjd::DevGrid> keep_codes = gcodes_;
-  std::vector<int> keep_schemes = gschemes_;
-  group_mode_ = false;
-  group_pending_ = false;
-  group_handle_ = nullptr;
-  gcodes_.clear();
-  gschemes_.clear();
-  gkeys_.clear();
-  if (!group_allowed_ || nitems_ < 1 || nitems_ > kGroupItems) return false;
-  bool reuse = keep_handle != nullptr;
-  if (reuse) {
-    gkeys_ = keep_keys;
-    gcodes_ = keep_codes;
-    gschemes_ = keep_schemes;
+  std::vector<std::string> keys(nitems_);
+  std::vector<hjd::DevGrid> grids(nitems_);
+  bool ok = group_allowed_ && nitems_ >= 1 && nitems_ <= kGroupItems;
+  for (int i = 0; ok && i < nitems_; ++i) {
+    const Slot& s = slots_[order_[i]];
+    grids[i] = hja::devgrid(s.g);
+    grids[i].tile_rows = 0;
+    keys[i] = hjk::code_key(grids[i], s.scheme);
   }
+  std::vector<int> pos(nitems_, -1);
+  bool reuse = ok && group_mode_ && group_handle_ != nullptr;
+  if (reuse) {
+    std::vector<bool> taken(gkeys_.size(), false);
+    for (int i = 0; i < nitems_ && reuse; ++i) {
+      for (size_t p = 0; p < gkeys_.size(); ++p)
+        if (!taken[p] && gkeys_[p] == keys[i]) {
+          pos[i] = (int)p;
+          taken[p] = true;
+          break;
+        }
+      reuse = pos[i] >= 0;
+    }
+  }
+  if (!reuse) {
+    group_mode_ = false;
+    group_pending_ = false;
+    group_handle_ = nullptr;
+    gkeys_.clear();
+    gcodes_.clear();
+    gschemes_.clear();
+    if (!ok) return false;
+    gkeys_ = keys;
+    gcodes_ = grids;
+    for (int i = 0; i < nitems_; ++i) {
+      gschemes_.push_back(slots_[order_[i]].scheme);
+      pos[i] = i;
+    }
+  }
+  // the pack: position p holds current item i with pos[i] == p, or nothing
   std::memset(&gpack_, 0, sizeof(gpack_));
-  std::vector<std::string>& keys = gkeys_;
+  int npos = (int)gkeys_.size();
+  std::vector<int> at(npos, -1);
+  for (int i = 0; i < nitems_; ++i) at[pos[i]] = i;
   unsigned blocks = 0;
-  for (int i = 0; i < nitems_; ++i) {
-    int k = order_[i];
+  for (int p = 0; p < npos; ++p) {
+    GroupItem& it = gpack_.items[p];
+    gpack_.block_begin[p] = (int)blocks;
+    if (at[p] < 0) continue;  // no grid here: no blocks
+    int k = order_[at[p]];
     const Slot& s = slots_[k];
     hj_grid g = s.g;
-    hjd::DevGrid d = hja::devgrid(g);
-    d.tile_rows = 0;
-    std::string key = hjk::code_key(d, s.scheme);
-    int code = -1;
-    for (size_t c = 0; c < keys.size(); ++c)
-      if (keys[c] == key) code = (int)c;
-    if (code < 0) {
-      reuse = false;
-      code = (int)keys.size();
-      keys.push_back(key);
-      gcodes_.push_back(d);
-      gschemes_.push_back(s.scheme);
-    }
-    GroupItem& it = gpack_.items[i];
-    it.g = d;
+    it.g = grids[at[p]];
     float dt = (float)s.dt;
     it.a[0] = hjd::StageArgs{g->W, g->W, g->A, nullptr, nullptr, dt, 0, s.clamp, s.band, s.margin};
     it.a[1] = hjd::StageArgs{g->A, g->W, g->B, nullptr, nullptr, dt, 0, s.clamp, s.band, s.margin};
     it.a[2] = hjd::StageArgs{g->B, g->W, g->W, g->snap, nullptr, dt, 0, s.clamp, s.band, s.margin};
     it.slot = k;
-    it.code = code;
-    it.bx = (d.plane + kGroupThreads - 1) / kGroupThreads;
-    gpack_.block_begin[i] = (int)blocks;
-    blocks += (unsigned)it.bx * (unsigned)(d.ndim == 4 ? d.n[0] : 1);
+    it.bx = (it.g.plane + kGroupThreads - 1) / kGroupThreads;
+    blocks += (unsigned)it.bx * (unsigned)(it.g.ndim == 4 ? it.g.n[0] : 1);
   }
-  gpack_.count = nitems_;
-  gpack_.block_begin[nitems_] = (int)blocks;
+  gpack_.count = npos;
+  gpack_.block_begin[npos] = (int)blocks;
   gblocks_ = blocks;
-  if (reuse) {
-    group_handle_ = keep_handle;
-    group_mode_ = true;
-    return true;
-  }
+  if (reuse) return true;
   group_mode_ = hjk::group_prepare(gcodes_, gschemes_, kGroupThreads, &group_handle_);
   group_pending_ = !group_mode_ && hjk::jit_enabled();
   return group_mode_;

@@ -20,15 +20,15 @@ struct Ctl {
   float last_resid;
 };
 
-// One grid of a group launch: bx blocks of kGroupThreads nodes per slab of
-// the flat mapping (by slabs: the first axis of a 4-D grid, else one);
-// `code` selects the body of the group kernel compiled for its kind, shape
-// and model constants.
+// One position of a group launch: a grid with bx blocks of kGroupThreads
+// nodes per slab of the flat mapping (slabs: the first axis of a 4-D grid,
+// else one).  The group kernel holds one body per position, compiled for
+// that grid's kind, shape and model constants.  A position without a grid
+// has bx = 0 (no blocks).
 struct GroupItem {
   hjd::DevGrid g;
   hjd::StageArgs a[3];  // stage 1..3 arguments (check and resid are set on the device)
   int slot;             // index into the control array
-  int code;
   int bx;
 };
 
@@ -40,32 +40,33 @@ struct GroupPack {
   GroupItem items[kGroupItems];
 };
 
-// The block's item of a group launch: its index (binary search over the
-// block offsets), its block (bx, yb) in the item's flat mapping, and its
-// stage arguments with the window check of stage 3 decided from the control
-// state.  -1 when the grid no longer steps (the whole block returns).
+// The block's position in a group launch: its index k (binary search over
+// the block offsets; positions without blocks are never found), its block
+// (bx, yb) in that grid's flat mapping, its control slot, and whether this
+// stage-3 launch closes the grid's window.  -1 when the grid no longer
+// steps (the whole block returns).  The kernel then reads the descriptor
+// and stage arguments of position k with a literal index, so that they
+// stay constant-bank operands as in the single-grid kernel.
 template <int STAGE>
-__device__ __forceinline__ int group_find(const GroupPack& pack, Ctl* ctl, hjd::StageArgs& a,
-                                          int& bx, int& yb, bool& check) {
+__device__ __forceinline__ int group_locate(const GroupPack& pack, const Ctl* ctl, int& bx,
+                                            int& yb, bool& check, int& slot) {
   int lo = 0, hi = pack.count - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
     if (pack.block_begin[mid] <= (int)blockIdx.x) lo = mid;
     else hi = mid - 1;
   }
-  const GroupItem& it = pack.items[lo];
-  const Ctl& c = ctl[it.slot];
+  slot = pack.items[lo].slot;
+  const Ctl& c = ctl[slot];
   if (!c.active) return -1;
+  int per = pack.items[lo].bx;
   int lb = (int)blockIdx.x - pack.block_begin[lo];
-  yb = lb / it.bx;
-  bx = lb - yb * it.bx;
-  a = it.a[STAGE - 1];
+  yb = lb / per;
+  bx = lb - yb * per;
   check = false;
   if (STAGE == 3) {
     long long s1 = c.steps + 1;
     check = (s1 % c.per == 0) || (s1 >= c.max_steps);
-    a.check = check ? 1 : 0;
-    a.resid = &ctl[it.slot].resid;
   }
   return lo;
 }

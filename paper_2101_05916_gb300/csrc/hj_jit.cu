@@ -79,7 +79,7 @@ const Nvrtc& nvrtc() {
 // model constants that stay fixed while a grid is updated (the disturbance
 // bound, alpha and the constraint box stay run-time values).
 struct Key {
-  int device, ndim, model, scheme, threads, tile_rows, con_kind;
+  int device, ndim, model, scheme, threads, tile_rows, local, con_kind;
   unsigned con_mask;
   int n[hjd::MAXD];
   unsigned geom[5 * hjd::MAXD];  // float bits of lo, h, ih, hih, wfloor
@@ -127,7 +127,7 @@ bool enabled() {
   return e == 1;
 }
 
-Key key_of(const hjd::DevGrid& g, int scheme, int threads) {
+Key key_of(const hjd::DevGrid& g, int scheme, int threads, bool local = false) {
   Key k;
   std::memset(&k, 0, sizeof(k));
   cudaGetDevice(&k.device);
@@ -136,6 +136,7 @@ Key key_of(const hjd::DevGrid& g, int scheme, int threads) {
   k.scheme = scheme;
   k.threads = threads;
   k.tile_rows = g.tile_rows;
+  k.local = local && g.tile_rows <= 0 ? 1 : 0;
   k.con_kind = g.con_kind;
   k.con_mask = g.con_mask;
   for (int d = 0; d < g.ndim; ++d) {
@@ -185,7 +186,7 @@ int radius_of(int scheme) { return scheme == 5 ? 3 : (scheme == 2 ? 2 : 1); }
 
 // The stage kernels of stage_kernel (hj_kernels.cu) with the shape fields
 // of the grid descriptor replaced by literals.
-std::string source(const hjd::DevGrid& g, int scheme, int threads) {
+std::string source(const hjd::DevGrid& g, int scheme, int threads, bool local) {
   std::string s = "#include \"hj_stage.cuh\"\n";
   s += fixed_fn("hj_fixed", g);
   char buf[256];
@@ -212,43 +213,48 @@ std::string source(const hjd::DevGrid& g, int scheme, int threads) {
                   "hj_stage_%d(const hjd::DevGrid g, const hjd::StageArgs a) {\n",
                   threads, st);
     s += buf;
-    std::snprintf(buf, sizeof(buf), "  hjd::flat_body<%d, %d, %d, %d>(hj_fixed(g), a);\n}\n",
-                  g.ndim, scheme, g.model, st);
+    std::snprintf(buf, sizeof(buf), "  hjd::flat_body<%d, %d, %d, %d, %s>(hj_fixed(g), a);\n}\n",
+                  g.ndim, scheme, g.model, st, local ? "true" : "false");
     s += buf;
   }
   return s;
 }
 
 // The group kernels of a batch: one kernel per RK stage over the blocks of
-// every grid in a hjb::GroupPack (the flat mapping, `threads` per block).
-// Each distinct (kind, shape, model constants) is one `code` with its own
-// specialised body; a block finds its grid, returns if that grid no longer
-// steps, and runs the body of its code.
-std::string group_source(const std::vector<hjd::DevGrid>& codes, const std::vector<int>& schemes,
+// every position of a hjb::GroupPack (the flat mapping, `threads` per
+// block).  Position i holds a grid like grids[i] (kind, shape and model
+// constants folded in) run with schemes[i]; its body reads the position's
+// descriptor and stage arguments with a literal index.
+std::string group_source(const std::vector<hjd::DevGrid>& grids, const std::vector<int>& schemes,
                          int threads) {
   std::string s = "#include \"hj_group.cuh\"\n";
-  for (size_t c = 0; c < codes.size(); ++c) s += fixed_fn("hj_fixed_" + std::to_string(c), codes[c]);
-  char buf[512];
+  for (size_t c = 0; c < grids.size(); ++c) s += fixed_fn("hj_fixed_" + std::to_string(c), grids[c]);
+  char buf[768];
   for (int st = 1; st <= 3; ++st) {
     std::snprintf(buf, sizeof(buf),
                   "extern \"C\" __global__ void __launch_bounds__(%d)\n"
                   "hj_group_%d(const __grid_constant__ hjb::GroupPack pack, hjb::Ctl* ctl) {\n"
-                  "  hjd::StageArgs a;\n  int bx, yb;\n  bool check;\n"
-                  "  int k = hjb::group_find<%d>(pack, ctl, a, bx, yb, check);\n"
+                  "  int bx, yb, slot;\n  bool check;\n"
+                  "  int k = hjb::group_locate<%d>(pack, ctl, bx, yb, check, slot);\n"
                   "  if (k < 0) return;\n  unsigned r = 0u;\n"
                   "  const int q = bx * %d + (int)threadIdx.x;\n"
-                  "  switch (pack.items[k].code) {\n",
+                  "  switch (k) {\n",
                   threads, st, st, threads);
     s += buf;
-    for (size_t c = 0; c < codes.size(); ++c) {
+    for (size_t c = 0; c < grids.size(); ++c) {
       std::snprintf(buf, sizeof(buf),
-                    "    case %d: r = hjd::stage_point<%d, %d, %d, %d>(hj_fixed_%d(pack.items[k].g),"
-                    " a, q, yb, check); break;\n",
-                    (int)c, codes[c].ndim, schemes[c], codes[c].model, st, (int)c);
+                    "    case %d: {\n"
+                    "      hjd::StageArgs a = pack.items[%d].a[%d];\n"
+                    "      a.check = check ? 1 : 0;\n      a.resid = &ctl[slot].resid;\n"
+                    "      r = hjd::stage_point<%d, %d, %d, %d>(hj_fixed_%d(pack.items[%d].g),"
+                    " a, q, yb, check);\n      break;\n    }\n",
+                    (int)c, (int)c, st - 1, grids[c].ndim, schemes[c], grids[c].model, st, (int)c,
+                    (int)c);
       s += buf;
     }
     s += "  }\n";
-    s += st == 3 ? "  if (check) hjd::block_max_bits(r, a.resid);\n}\n" : "  (void)r;\n}\n";
+    s += st == 3 ? "  if (check) hjd::block_max_bits(r, &ctl[slot].resid);\n}\n"
+                 : "  (void)r;\n}\n";
   }
   return s;
 }
@@ -354,8 +360,8 @@ bool capturing(cudaStream_t s) {
 
 // The entry of (grid shape, scheme, threads): started on first sight,
 // loaded once compiled when `may_load`.  Returns it when loaded.
-Entry* lookup(const hjd::DevGrid& g, int scheme, int threads, bool may_load) {
-  Key k = key_of(g, scheme, threads);
+Entry* lookup(const hjd::DevGrid& g, int scheme, int threads, bool may_load, bool local = false) {
+  Key k = key_of(g, scheme, threads, local);
   std::shared_ptr<Entry> e;
   {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -367,7 +373,7 @@ Entry* lookup(const hjd::DevGrid& g, int scheme, int threads, bool may_load) {
         e->state.store(3);
         return nullptr;
       }
-      compile_async(e, source(g, scheme, threads));
+      compile_async(e, source(g, scheme, threads, k.local != 0));
       return nullptr;
     }
     e = it->second;
@@ -453,7 +459,8 @@ cudaError_t jit_launch(const hjd::DevGrid& g, int scheme, int stage, const hjd::
                        cudaStream_t s, int threads, bool* used) {
   *used = false;
   if (!jit_wanted(g)) return cudaSuccess;
-  Entry* e = lookup(g, scheme, threads, !capturing(s));
+  bool local = a.tiles || a.live || a.slab_resid;
+  Entry* e = lookup(g, scheme, threads, !capturing(s), local);
   if (!e) return cudaSuccess;
   dim3 grid, block;
   if (g.tile_rows > 0) {
@@ -533,7 +540,7 @@ static hj_status jit_check(int ndim, const int* n, int model, int scheme, int th
     return hja::fail(HJ_ERR_ARG, "row tile does not fit the grid");
   if (!hjk::nvrtc().ok) return hja::fail(HJ_ERR_CUDA, "NVRTC could not be loaded");
   std::string log;
-  std::vector<char> cubin = hjk::compile(hjk::source(d, scheme, threads), &log);
+  std::vector<char> cubin = hjk::compile(hjk::source(d, scheme, threads, false), &log);
   if (cubin.empty()) return hja::fail(HJ_ERR_CUDA, "NVRTC: %.400s", log.c_str());
   return HJ_OK;
 }

@@ -31,10 +31,13 @@ std::atomic<unsigned long long> g_launches{0};
 using hjd::DevGrid;
 using hjd::StageArgs;
 
-template <int D, int S, int M, int STAGE, int THREADS>
+template <int D, int S, int M, int STAGE, int THREADS, bool LOCAL>
 __global__ void __launch_bounds__(THREADS) stage_kernel(const DevGrid g, const StageArgs a) {
-  hjd::flat_body<D, S, M, STAGE>(g, a);
+  hjd::flat_body<D, S, M, STAGE, LOCAL>(g, a);
 }
+
+// Whether a stage launch is part of a localized solve.
+static bool is_local(const StageArgs& a) { return a.tiles || a.live || a.slab_resid; }
 
 // Row-tile variant: block b stages lines [b R, b R + R) of the fastest axis
 // in shared memory (hjd::stage_tile) and computes their nodes.
@@ -186,13 +189,13 @@ static dim3 stage_grid(const DevGrid& g, int threads) {
   return dim3(bx, by, 1u);
 }
 
-template <int D, int S, int M, int T>
+template <int D, int S, int M, int T, bool LOCAL>
 static void stage_launch(const DevGrid& g, int stage, const StageArgs& a, cudaStream_t s) {
   dim3 grid = a.tiles ? dim3((unsigned)a.ntiles, 1u, 1u) : stage_grid(g, T), block(T);
   switch (stage) {
-    case 1: stage_kernel<D, S, M, 1, T><<<grid, block, 0, s>>>(g, a); break;
-    case 2: stage_kernel<D, S, M, 2, T><<<grid, block, 0, s>>>(g, a); break;
-    default: stage_kernel<D, S, M, 3, T><<<grid, block, 0, s>>>(g, a); break;
+    case 1: stage_kernel<D, S, M, 1, T, LOCAL><<<grid, block, 0, s>>>(g, a); break;
+    case 2: stage_kernel<D, S, M, 2, T, LOCAL><<<grid, block, 0, s>>>(g, a); break;
+    default: stage_kernel<D, S, M, 3, T, LOCAL><<<grid, block, 0, s>>>(g, a); break;
   }
 }
 
@@ -219,10 +222,15 @@ static cudaError_t stage_dispatch(const DevGrid& g, int stage, const StageArgs& 
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
   }
-  switch (threads) {
-    case 128: stage_launch<D, S, M, 128>(g, stage, a, s); break;
-    case 512: stage_launch<D, S, M, 512>(g, stage, a, s); break;
-    default: stage_launch<D, S, M, 256>(g, stage, a, s); break;
+  if (is_local(a)) {
+    // localized solves launch 256-thread blocks of the flat mapping
+    stage_launch<D, S, M, 256, true>(g, stage, a, s);
+  } else {
+    switch (threads) {
+      case 128: stage_launch<D, S, M, 128, false>(g, stage, a, s); break;
+      case 512: stage_launch<D, S, M, 512, false>(g, stage, a, s); break;
+      default: stage_launch<D, S, M, 256, false>(g, stage, a, s); break;
+    }
   }
   g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
@@ -270,6 +278,7 @@ bool tile_ok(const DevGrid& g, int tile_rows, const void* const* fields, int nfi
 cudaError_t launch_stage(const DevGrid& g, int scheme, int stage, const StageArgs& a, cudaStream_t s,
                          int threads, bool allow_jit) {
   if (threads != 128 && threads != 512) threads = 256;
+  if (g.tile_rows <= 0 && is_local(a)) threads = 256;
   if (g.tile_rows > 0 && (reinterpret_cast<uintptr_t>(a.src) & 15u)) return cudaErrorInvalidValue;
   if (a.tiles && a.ntiles == 0) return cudaSuccess;
   if (allow_jit) {

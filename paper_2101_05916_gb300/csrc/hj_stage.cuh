@@ -47,8 +47,10 @@ __device__ __forceinline__ void coords(const DevGrid& g, const int (&idx)[D], fl
 //   3: W3 = 1/3 W + 2/3 (W2 + dt L(W2)),  W <- min(W3, l)  [, W_prev]
 // fast: the node's fastest-axis line in shared memory (see lf_rhs), or null.
 // Returns the window-residual contribution |W_new - snap| as float bits
-// (stage 3 with check; 0 otherwise).
-template <int D, int S, int M, int STAGE>
+// (stage 3 with check; 0 otherwise).  LOCAL compiles in what a localized
+// solve needs (frozen slabs, the slab residual in *raw, mid-window checks);
+// plain solves run without it.
+template <int D, int S, int M, int STAGE, bool LOCAL = false>
 __device__ __forceinline__ unsigned stage_node(const DevGrid& g, const StageArgs& a,
                                                const int (&idx)[D], int p, bool check,
                                                const float* fast, unsigned* raw = nullptr) {
@@ -66,7 +68,9 @@ __device__ __forceinline__ unsigned stage_node(const DevGrid& g, const StageArgs
     return 0u;
   } else {
     // a frozen slab of a localized solve keeps W and its snapshot
-    if (a.live && !a.live[slab_of<D>(g, idx)]) return 0u;
+    if constexpr (LOCAL) {
+      if (a.live && !a.live[slab_of<D>(g, idx)]) return 0u;
+    }
     float w = a.base[p];
     float w3 = fmaf(1.f / 3.f, w, (2.f / 3.f) * stepped);
     float wn = fminf(w3, margin<D>(g, x, p));
@@ -74,9 +78,11 @@ __device__ __forceinline__ unsigned stage_node(const DevGrid& g, const StageArgs
     if (w3 != w3) wn = w3;  // keep a NaN visible to the stop test
     a.dst[p] = wn;
     if (!check) return 0u;
+    // check 1 closes a window (the snapshot moves on); check 2 is a
+    // localized solve's mid-window look at the change since the window began
     float sv = a.snap[p];
     float r = fabsf(wn - sv);
-    a.snap[p] = wn;
+    if (!LOCAL || a.check != 2) a.snap[p] = wn;
     if (a.margin > 0) {
       // only faces of unconstrained axes: on a constrained axis the margin l
       // decides the value next to the face
@@ -88,7 +94,9 @@ __device__ __forceinline__ unsigned stage_node(const DevGrid& g, const StageArgs
     }
     // the slab residual of a localized solve: every node away from the
     // faces the margin excludes, inside the band or not
-    if (raw) *raw = __float_as_uint(r);
+    if constexpr (LOCAL) {
+      if (raw) *raw = __float_as_uint(r);
+    }
     if (a.band > 0.f && fminf(fabsf(wn), fabsf(sv)) > a.band) r = 0.f;
     if (wn != wn) r = wn;  // NaN always reaches the stop test
     return __float_as_uint(r);
@@ -127,13 +135,21 @@ __device__ __forceinline__ int flat_blocks_per_slab(const DevGrid& g) {
   return (g.plane + (int)blockDim.x - 1) / (int)blockDim.x;
 }
 
-// Body of a flat stage kernel.  Without a tile list, block (x, y) covers
-// nodes x * blockDim .. of slab y; with one, block b runs flat tile
-// tiles[b] = y * (blocks per slab) + x.  Stage 3 with check folds the
-// stop-test residual of the block into *a.resid and, in a localized solve,
-// every node's change into its slab's entry of a.slab_resid.
-template <int D, int S, int M, int STAGE>
+// Body of a flat stage kernel.  Block (x, y) covers nodes x * blockDim ..
+// of slab y; stage 3 with check folds the stop-test residual of the block
+// into *a.resid.  The LOCAL variant (localized solves) also takes a tile
+// list, where block b runs flat tile tiles[b] = y * (blocks per slab) + x,
+// and folds every node's change into its slab's entry of a.slab_resid.
+template <int D, int S, int M, int STAGE, bool LOCAL>
 __device__ __forceinline__ void flat_body(const DevGrid& g, const StageArgs& a) {
+  if constexpr (!LOCAL) {
+    unsigned r = stage_point<D, S, M, STAGE>(g, a, blockIdx.x * blockDim.x + threadIdx.x,
+                                             blockIdx.y, a.check != 0);
+    if constexpr (STAGE == 3) {
+      if (a.check) block_max_bits(r, a.resid);
+    }
+    return;
+  }
   int bx = (int)blockIdx.x, yb = (int)blockIdx.y;
   if (a.tiles) {
     int t = a.tiles[blockIdx.x];
@@ -146,12 +162,12 @@ __device__ __forceinline__ void flat_body(const DevGrid& g, const StageArgs& a) 
   int p;
   if (node_of<D>(g, bx * (int)blockDim.x + (int)threadIdx.x, yb, idx, p)) {
     o.slab = slab_of<D>(g, idx);
-    o.resid = stage_node<D, S, M, STAGE>(g, a, idx, p, a.check != 0, nullptr, &o.raw);
+    o.resid = stage_node<D, S, M, STAGE, true>(g, a, idx, p, a.check != 0, nullptr, &o.raw);
   }
   if constexpr (STAGE == 3) {
     if (a.check) {
       if (a.slab_resid) slab_max_bits(o.slab, o.raw, a.slab_resid);
-      block_max_bits(o.resid, a.resid);
+      if (a.check != 2) block_max_bits(o.resid, a.resid);
     }
   }
 }
@@ -245,7 +261,8 @@ __device__ __forceinline__ TileOut stage_tile(const DevGrid& g, const StageArgs&
     }
   }
   out.slab = slab_of<D>(g, idx);
-  out.resid = stage_node<D, S, M, STAGE>(g, a, idx, base + t, check, sm + r * P + R + idx[D - 1],
+  out.resid = stage_node<D, S, M, STAGE, true>(g, a, idx, base + t, check,
+                                               sm + r * P + R + idx[D - 1],
                                          &out.raw);
   return out;
 }
@@ -261,7 +278,7 @@ __device__ __forceinline__ void tile_body(const DevGrid& g, const StageArgs& a, 
   if constexpr (STAGE == 3) {
     if (a.check) {
       if (a.slab_resid) slab_max_bits(o.slab, o.raw, a.slab_resid);
-      block_max_bits(o.resid, a.resid);
+      if (a.check != 2) block_max_bits(o.resid, a.resid);
     }
   }
 }
