@@ -67,9 +67,9 @@ FLOPS_PER_UPDATE = {("quad_x4", 5): 1624.0}
 BYTES_PER_UPDATE = 32.0
 # DRAM bytes (read + write) per stage launch, averaged over stages 1-3, from
 # one ncu capture of the stage kernels on the 81^4 grid (three consecutive
-# launches, --clock-control none).  None until the current kernel has been
-# captured; reset to None whenever the stage kernel changes.
-STAGE_TRAFFIC_BYTES_81 = None
+# launches of the second step, --clock-control none): 307.4, 491.3 and
+# 480.2 MB.  Reset to None whenever the stage kernel changes.
+STAGE_TRAFFIC_BYTES_81 = 426310912.0
 # The same for the 41^4 grid.
 STAGE_TRAFFIC_BYTES_41 = None
 FP32_LANES_PER_SM = 128

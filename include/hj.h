@@ -111,9 +111,9 @@ typedef struct {
                          /* only slabs whose value changed by more than local_tol in the  */
                          /* last window (nodes within band_margin of a free face do not   */
                          /* count; nodes outside the band do), and slabs close enough to  */
-                         /* them for a change to arrive before the masks are refreshed    */
-                         /* (four times a window; the CFL distance of a quarter window    */
-                         /* along each slab axis, plus local_margin slabs), step;         */
+                         /* them for a change to arrive within the next window (the CFL   */
+                         /* distance of a window along each slab axis, plus               */
+                         /* local_margin slabs), step;                                    */
                          /* the others keep their value.  Slabs are the lines of the two  */
                          /* slowest axes of a 4-D grid, the first axis of a 2-D or 3-D    */
                          /* grid.  Stage values next to stepping slabs are recomputed on  */
@@ -529,6 +529,31 @@ hj_status hj_jit_check_tiles(int ndim, const int* n, int model, int scheme, int 
  * the kernels a batch runs once they are compiled for its composition. */
 hj_status hj_jit_check_group(int ngrids, const int* ndims, const int* shapes, const int* models,
                              const int* schemes);
+
+/* Device memory allocator hook (no counterpart in the paper: an interop
+ * convention of the boundary).  By default the library allocates its
+ * device memory with cudaMalloc and returns it with cudaFree.  A caller
+ * whose device memory belongs to a pool (PyTorch's caching allocator, for
+ * one) can route those allocations through it instead:
+ *   - alloc(bytes, device, user) returns `bytes` of device memory on
+ *     `device` (the current device at the call), aligned to at least 256
+ *     bytes, or NULL when it has none; free(ptr, device, user) takes it back.
+ *   - The hook in force when a grid, a server or a batch is created serves
+ *     all of that object's device allocations, including the ones made
+ *     later (stage fields, disturbance and constraint fields, query and
+ *     filter staging) and their release at destroy.  Pinned host buffers
+ *     are not affected.
+ *   - hj_set_allocator(NULL, NULL, NULL) restores cudaMalloc / cudaFree for
+ *     objects created afterwards.  Giving only one of the two functions is
+ *     HJ_ERR_ARG.
+ *   - The hook may be called from the server's worker thread.  The library
+ *     synchronises the object's stream before it frees memory, so a pool
+ *     that reuses freed blocks on another stream sees no pending work.
+ * A NULL from alloc makes the call that needed the memory fail with
+ * HJ_ERR_OOM. */
+typedef void* (*hj_alloc_fn)(size_t bytes, int device, void* user);
+typedef void (*hj_free_fn)(void* ptr, int device, void* user);
+hj_status hj_set_allocator(hj_alloc_fn alloc, hj_free_fn free_fn, void* user);
 
 /* Number of nodes of the grid. */
 long long hj_grid_points(hj_grid g);

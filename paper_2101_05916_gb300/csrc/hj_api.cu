@@ -11,6 +11,7 @@
 // A window is captured once as a CUDA graph and replayed, so the launch cost
 // of the many small kernels of a 2-D grid is paid once per graph.
 #include <algorithm>
+#include <cstdint>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -25,6 +26,42 @@
 #include "hj_grid.h"
 
 namespace hja {
+
+static std::mutex g_alloc_mu;
+static Allocator g_alloc;
+
+Allocator current_allocator() {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  return g_alloc;
+}
+
+cudaError_t dev_malloc(const Allocator& a, void** p, size_t bytes) {
+  *p = nullptr;
+  if (!a.alloc) return cudaMalloc(p, bytes);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  *p = a.alloc(bytes, dev, a.user);
+  if (!*p) return cudaErrorMemoryAllocation;
+  // fields are 256-byte aligned plus guard floats, and tiles load 16 bytes
+  if (reinterpret_cast<uintptr_t>(*p) & 255u) {
+    a.free(*p, dev, a.user);
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaSuccess;
+}
+
+void dev_free(const Allocator& a, void* p) {
+  if (!p) return;
+  if (!a.free) {
+    cudaFree(p);
+    return;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+  a.free(p, dev, a.user);
+}
 
 static thread_local char t_err[1024] = "";
 
@@ -376,49 +413,45 @@ static float bits_to_float(unsigned b) {
 //     and the rings on which stages 1 and 2 are recomputed (2 and 1
 //     stencil radii further), and a list kernel turns them into the row
 //     tiles of each stage;
-//   - the next steps launch exactly those tiles; stage 3 commits only
-//     stepping slabs, the others keep W and their snapshot;
-//   - the masks are also refreshed three times inside each window, from the
-//     change since the window began, so that the distance a change can
-//     travel before the next refresh (and with it the margins) stays small.
+//   - the next window launches exactly those tiles; stage 3 commits only
+//     stepping slabs, the others keep W and their snapshot.
 // The stop test is the usual one over the nodes that step.  One read-back
 // per window carries the residual and the three list lengths.
 hj_status solve_local(hj_grid g, const hj_solve_opts& o, double dt, hj_solve_stats& stats,
                       std::chrono::steady_clock::time_point t0) {
   hjd::DevGrid d = devgrid(g);
-  int t = g->tile_rows > 0 ? 256 : g->threads;
+  // localized launches of the flat mapping use 256-thread blocks
+  const int t = 256;
   hjk::LocalLayout L = hjk::local_layout(d, t);
   if (g->local_slabs != L.nslabs || g->local_tiles != L.ntiles) {
-    cudaFree(g->slab_resid);
-    cudaFree(g->slab_masks);
-    cudaFree(g->tile_lists);
+    hja::dev_free(g->alloc, g->slab_resid);
+    hja::dev_free(g->alloc, g->slab_masks);
+    hja::dev_free(g->alloc, g->tile_lists);
     g->slab_resid = nullptr;
     g->slab_masks = nullptr;
     g->tile_lists = nullptr;
     g->local_slabs = g->local_tiles = 0;
-    HJ_CU(cudaMalloc(&g->slab_resid, (size_t)L.nslabs * sizeof(unsigned)));
-    HJ_CU(cudaMalloc(&g->slab_masks, 3 * (size_t)L.nslabs));
-    HJ_CU(cudaMalloc(&g->tile_lists, 3 * (size_t)L.ntiles * sizeof(int)));
+    HJ_CU(hja::dev_malloc(g->alloc, (void**)&g->slab_resid, (size_t)L.nslabs * sizeof(unsigned)));
+    HJ_CU(hja::dev_malloc(g->alloc, (void**)&g->slab_masks, 3 * (size_t)L.nslabs));
+    HJ_CU(hja::dev_malloc(g->alloc, (void**)&g->tile_lists, 3 * (size_t)L.ntiles * sizeof(int)));
     g->local_slabs = L.nslabs;
     g->local_tiles = L.ntiles;
   }
-  if (!g->tile_counts) HJ_CU(cudaMalloc(&g->tile_counts, 4 * sizeof(int)));
+  if (!g->tile_counts) HJ_CU(hja::dev_malloc(g->alloc, (void**)&g->tile_counts, 4 * sizeof(int)));
   if (!g->tile_counts_h) HJ_CU(cudaMallocHost(&g->tile_counts_h, 4 * sizeof(int)));
   cudaStream_t s = g->stream;
   const float fdt = (float)dt;
   long long per = (long long)std::ceil(o.check_dt / dt - 1e-9);
   if (per < 1) per = 1;
-  // the masks are refreshed every `sub` steps (four times a window); how
-  // far (in slabs) a change can travel along each slab axis in that time:
-  // the CFL speed alpha_a dt / h_a cells per step times the steps, plus the
-  // caller's margin
-  long long sub = std::max(1ll, (per + 3) / 4);
+  // how far (in slabs) a change can travel along each slab axis in one
+  // window: the CFL speed alpha_a dt / h_a cells per step times the steps,
+  // plus the caller's margin
   int kax[2] = {0, 0};
   for (int q = 0; q < 2; ++q) {
     int ax = q;  // slab axes: 0 and 1 of a 4-D grid, 0 of a 2-D or 3-D grid
     int slab_axes = g->ndim == 4 ? 2 : (g->ndim >= 2 ? 1 : 0);
     if (ax >= slab_axes) continue;
-    double cells = (double)sub * (double)g->alpha[ax] * dt / g->h[ax];
+    double cells = (double)per * (double)g->alpha[ax] * dt / g->h[ax];
     kax[q] = (int)std::ceil(cells) + 1 + o.local_margin;
   }
   int counts[3] = {L.ntiles, L.ntiles, L.ntiles};
@@ -448,29 +481,11 @@ hj_status solve_local(hj_grid g, const hj_solve_opts& o, double dt, hj_solve_sta
     for (long long i = 0; i < todo; ++i) {
       HJ_CU(hjk::launch_stage(d, o.scheme, 1, a1, s, t));
       HJ_CU(hjk::launch_stage(d, o.scheme, 2, a2, s, t));
-      bool refresh = (i + 1) % sub == 0 && i != todo - 1;
-      a3.check = (i == todo - 1) ? 1 : (refresh ? 2 : 0);
+      a3.check = (i == todo - 1) ? 1 : 0;
       HJ_CU(hjk::launch_stage(d, o.scheme, 3, a3, s, t));
-      tiles_run += (double)(counts[0] + counts[1] + counts[2]);
-      tiles_full += 3.0 * L.ntiles;
-      if (refresh) {
-        // mid-window refresh of the masks from the change since the window
-        // began; the rest of the window launches the lists that follow
-        HJ_CU(hjk::launch_local_lists(d, o.scheme, t, g->slab_resid, (float)o.local_tol, kax[0],
-                                      kax[1], g->slab_masks, g->tile_lists, g->tile_counts, s));
-        HJ_CU(cudaMemcpyAsync(g->tile_counts_h, g->tile_counts, 3 * sizeof(int),
-                              cudaMemcpyDeviceToHost, s));
-        HJ_CU(cudaStreamSynchronize(s));
-        for (int q = 0; q < 3; ++q) counts[q] = g->tile_counts_h[q];
-        a1.tiles = g->tile_lists;
-        a2.tiles = g->tile_lists + L.ntiles;
-        a3.tiles = g->tile_lists + 2 * L.ntiles;
-        a1.ntiles = counts[0];
-        a2.ntiles = counts[1];
-        a3.ntiles = counts[2];
-        a3.live = g->slab_masks;
-      }
     }
+    tiles_run += (double)todo * (counts[0] + counts[1] + counts[2]);
+    tiles_full += (double)todo * 3.0 * L.ntiles;
     HJ_CU(hjk::launch_local_lists(d, o.scheme, t, g->slab_resid, (float)o.local_tol, kax[0],
                                   kax[1], g->slab_masks, g->tile_lists, g->tile_counts, s));
     HJ_CU(cudaMemcpyAsync(g->hscal + 4, g->dscal + 4, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
@@ -507,6 +522,16 @@ extern "C" {
 
 const char* hj_last_error(void) { return t_err; }
 
+hj_status hj_set_allocator(hj_alloc_fn alloc, hj_free_fn free_fn, void* user) {
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return fail(HJ_ERR_ARG, "give both allocator functions or neither");
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc.alloc = alloc;
+  g_alloc.free = free_fn;
+  g_alloc.user = alloc ? user : nullptr;
+  return HJ_OK;
+}
+
 unsigned long long hj_kernel_launches(void) { return hjk::g_launches.load(); }
 
 long long hj_grid_points(hj_grid g) { return g ? g->npts : 0; }
@@ -536,17 +561,17 @@ void hj_grid_destroy(hj_grid g) {
     DeviceGuard dg(g->device);
     if (g->stream) cudaStreamSynchronize(g->stream);
     drop_graph(g);
-    for (int i = 0; i < 4; ++i) cudaFree(g->raw[i]);
-    cudaFree(g->tab);
-    cudaFree(g->dfield);
-    cudaFree(g->lfield);
-    cudaFree(g->dscal);
-    cudaFree(g->qbuf);
-    cudaFree(g->fdev);
-    cudaFree(g->slab_resid);
-    cudaFree(g->slab_masks);
-    cudaFree(g->tile_lists);
-    cudaFree(g->tile_counts);
+    for (int i = 0; i < 4; ++i) hja::dev_free(g->alloc, g->raw[i]);
+    hja::dev_free(g->alloc, g->tab);
+    hja::dev_free(g->alloc, g->dfield);
+    hja::dev_free(g->alloc, g->lfield);
+    hja::dev_free(g->alloc, g->dscal);
+    hja::dev_free(g->alloc, g->qbuf);
+    hja::dev_free(g->alloc, g->fdev);
+    hja::dev_free(g->alloc, g->slab_resid);
+    hja::dev_free(g->alloc, g->slab_masks);
+    hja::dev_free(g->alloc, g->tile_lists);
+    hja::dev_free(g->alloc, g->tile_counts);
     if (g->tile_counts_h) cudaFreeHost(g->tile_counts_h);
     if (g->fhost) cudaFreeHost(g->fhost);
     if (g->hscal) cudaFreeHost(g->hscal);
@@ -578,6 +603,7 @@ hj_status hj_grid_create(hj_grid* out, int ndim, const int* n, const double* lo,
   hj_grid g = new (std::nothrow) hj_grid_s();
   if (!g) return fail(HJ_ERR_OOM, "host allocation failed");
   g->device = dev;
+  g->alloc = current_allocator();
   g->ndim = ndim;
   g->npts = npts;
   for (int i = 0; i < ndim; ++i) {
@@ -592,7 +618,7 @@ hj_status hj_grid_create(hj_grid* out, int ndim, const int* n, const double* lo,
   bytes = (bytes + 255) & ~(size_t)255;
   cudaError_t e = cudaSuccess;
   for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
-    e = cudaMalloc(&g->raw[i], bytes);
+    e = hja::dev_malloc(g->alloc, (void**)&g->raw[i], bytes);
     if (e == cudaSuccess) e = cudaMemset(g->raw[i], 0, bytes);
   }
   if (e == cudaSuccess) {
@@ -601,7 +627,7 @@ hj_status hj_grid_create(hj_grid* out, int ndim, const int* n, const double* lo,
     g->B = g->raw[2] + kGuard;
     g->snap = g->raw[3] + kGuard;
   }
-  if (e == cudaSuccess) e = cudaMalloc(&g->dscal, 64 * sizeof(unsigned));
+  if (e == cudaSuccess) e = hja::dev_malloc(g->alloc, (void**)&g->dscal, 64 * sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMallocHost(&g->hscal, 64 * sizeof(unsigned));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
@@ -648,9 +674,9 @@ hj_status hj_set_dynamics(hj_grid g, int model, const double* params, int nparam
     int m = g->n[2];
     float* host = new float[m];
     for (int j = 0; j < m; ++j) host[j] = (float)(params[0] * std::tan(g->lo[2] + j * g->h[2]));
-    cudaFree(g->tab);
+    hja::dev_free(g->alloc, g->tab);
     g->tab = nullptr;
-    cudaError_t e = cudaMalloc(&g->tab, m * sizeof(float));
+    cudaError_t e = hja::dev_malloc(g->alloc, (void**)&g->tab, m * sizeof(float));
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(g->tab, host, m * sizeof(float), cudaMemcpyHostToDevice, g->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
@@ -664,7 +690,7 @@ hj_status hj_set_dynamics(hj_grid g, int model, const double* params, int nparam
 static void drop_lfield(hj_grid g) {
   if (g->lfield) {
     DeviceGuard dg(g->device);
-    cudaFree(g->lfield);
+    hja::dev_free(g->alloc, g->lfield);
     g->lfield = nullptr;
   }
 }
@@ -711,7 +737,7 @@ hj_status hj_set_constraint_field(hj_grid g, const float* l, int on_device) {
   if (!g || !l) return fail(HJ_ERR_ARG, "NULL argument");
   DeviceGuard dg(g->device);
   size_t n = (size_t)g->npts;
-  if (!g->lfield) HJ_CU(cudaMalloc(&g->lfield, n * sizeof(float)));
+  if (!g->lfield) HJ_CU(hja::dev_malloc(g->alloc, (void**)&g->lfield, n * sizeof(float)));
   cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   HJ_CU(cudaMemcpyAsync(g->lfield, l, n * sizeof(float), k, g->stream));
   HJ_CU(cudaMemsetAsync(g->dscal + 5, 0, sizeof(unsigned), g->stream));
@@ -755,10 +781,10 @@ hj_status hj_set_disturbance_field(hj_grid g, const float* d_lo, const float* d_
   DeviceGuard dg(g->device);
   size_t n = (size_t)nd * (size_t)g->npts;
   if (!g->dfield || g->dfield_nd != nd) {
-    cudaFree(g->dfield);
+    hja::dev_free(g->alloc, g->dfield);
     g->dfield = nullptr;
     g->dfield_nd = 0;
-    HJ_CU(cudaMalloc(&g->dfield, 2 * n * sizeof(float)));
+    HJ_CU(hja::dev_malloc(g->alloc, (void**)&g->dfield, 2 * n * sizeof(float)));
   }
   cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   HJ_CU(cudaMemcpyAsync(g->dfield, d_lo, n * sizeof(float), k, g->stream));
@@ -771,7 +797,7 @@ hj_status hj_set_disturbance_field(hj_grid g, const float* d_lo, const float* d_
   HJ_CU(cudaStreamSynchronize(g->stream));
   if (g->hscal[5]) {
     // the rejected values are gone with the buffer; no bound is in force now
-    cudaFree(g->dfield);
+    hja::dev_free(g->alloc, g->dfield);
     g->dfield = nullptr;
     g->dfield_nd = 0;
     g->nd = 0;
@@ -1011,10 +1037,10 @@ static hj_status query(hj_grid g, int npts, const double* x, double* out, int gr
   size_t nout = grad ? nin : (size_t)npts;
   size_t need = nin + nout;
   if (need > g->qcap) {
-    cudaFree(g->qbuf);
+    hja::dev_free(g->alloc, g->qbuf);
     g->qbuf = nullptr;
     g->qcap = 0;
-    HJ_CU(cudaMalloc(&g->qbuf, need * sizeof(double)));
+    HJ_CU(hja::dev_malloc(g->alloc, (void**)&g->qbuf, need * sizeof(double)));
     g->qcap = need;
   }
   HJ_CU(cudaMemsetAsync(g->dscal + 5, 0, sizeof(unsigned), g->stream));

@@ -128,21 +128,22 @@ __global__ void batch_control(const int* __restrict__ slots, int nitems, Ctl* ct
 // ------------------------------------------------------------------ host
 
 Runner::Runner(int device, cudaStream_t stream, int capacity)
-    : device_(device), stream_(stream), cap_(capacity), slots_(capacity) {}
+    : device_(device), stream_(stream), cap_(capacity), slots_(capacity),
+      alloc_(hja::current_allocator()) {}
 
 Runner::~Runner() {
   hja::DeviceGuard dg(device_);
   cudaStreamSynchronize(stream_);
   drop_graphs();
-  cudaFree(dev_ctl_);
-  cudaFree(dev_slots_);
+  hja::dev_free(alloc_, dev_ctl_);
+  hja::dev_free(alloc_, dev_slots_);
   if (host_ctl_) cudaFreeHost(host_ctl_);
   if (cap_stream_) cudaStreamDestroy(cap_stream_);
 }
 
 hj_status Runner::init() {
   hja::DeviceGuard dg(device_);
-  HJ_CU(cudaMalloc(&dev_ctl_, sizeof(Ctl) * cap_));
+  HJ_CU(hja::dev_malloc(alloc_, (void**)&dev_ctl_, sizeof(Ctl) * cap_));
   HJ_CU(cudaMallocHost(&host_ctl_, sizeof(Ctl) * cap_));
   std::memset(host_ctl_, 0, sizeof(Ctl) * cap_);
   HJ_CU(cudaMemsetAsync(dev_ctl_, 0, sizeof(Ctl) * cap_, stream_));
@@ -306,10 +307,10 @@ hj_status Runner::rebuild() {
   nitems_ = (int)order_.size();
   plan_group();
   if (nitems_ > item_cap_) {
-    cudaFree(dev_slots_);
+    hja::dev_free(alloc_, dev_slots_);
     dev_slots_ = nullptr;
     item_cap_ = std::max(nitems_, 2 * item_cap_);
-    HJ_CU(cudaMalloc(&dev_slots_, sizeof(int) * item_cap_));
+    HJ_CU(hja::dev_malloc(alloc_, (void**)&dev_slots_, sizeof(int) * item_cap_));
   }
   if (nitems_) {
     HJ_CU(cudaMemcpyAsync(dev_slots_, order_.data(), sizeof(int) * nitems_, cudaMemcpyHostToDevice,

@@ -92,6 +92,7 @@ class Runner {
   cudaStream_t stream_;
   int cap_;
   std::vector<Slot> slots_;
+  hja::Allocator alloc_;  // serves the control arrays
   Ctl* dev_ctl_ = nullptr;
   Ctl* host_ctl_ = nullptr;  // pinned mirror
   int* dev_slots_ = nullptr;   // control slots of the current items, in launch order

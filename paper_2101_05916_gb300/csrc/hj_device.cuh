@@ -71,8 +71,7 @@ struct StageArgs {
   float* snap;         // window snapshot (stage 3 with check)
   unsigned* resid;     // max |W - snap| as float bits (stage 3 with check)
   float dt;
-  int check;           // stage 3: 0 none; 1 window residual (and snapshot moves on);
-                       // 2 slab residual since the window began only (localized solves)
+  int check;           // stage 3: fold the window residual, move the snapshot on
   int clamp;           // 0: min(W3, l); 1: min(W3, l, W)
   float band;          // > 0: residual only where min(|W|, |snap|) <= band
   int margin;          // residual only at nodes >= margin cells from every face

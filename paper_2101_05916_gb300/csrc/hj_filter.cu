@@ -171,12 +171,12 @@ hj_status hj_safety_filter(const hj_grid* grids, int ngrids, const int* axes,
     size_t n_a = (n_w + 1) / 2;
     size_t need = n_s + n_u + n_w + n_a + 1;
     if (need > g0->fcap) {
-      cudaFree(g0->fdev);
+      hja::dev_free(g0->alloc, g0->fdev);
       if (g0->fhost) cudaFreeHost(g0->fhost);
       g0->fdev = nullptr;
       g0->fhost = nullptr;
       g0->fcap = 0;
-      HJ_CU(cudaMalloc(&g0->fdev, need * sizeof(double)));
+      HJ_CU(hja::dev_malloc(g0->alloc, (void**)&g0->fdev, need * sizeof(double)));
       HJ_CU(cudaMallocHost(&g0->fhost, need * sizeof(double)));
       g0->fcap = need;
     }

@@ -7,8 +7,24 @@
 #include "hj.h"
 #include "hj_internal.h"
 
+namespace hja {
+// The device allocator an object was created with (hj_set_allocator); both
+// null: cudaMalloc / cudaFree.
+struct Allocator {
+  hj_alloc_fn alloc = nullptr;
+  hj_free_fn free = nullptr;
+  void* user = nullptr;
+};
+Allocator current_allocator();
+// Device memory through the allocator (cudaErrorMemoryAllocation when it has
+// none); release through it (a null pointer is ignored).
+cudaError_t dev_malloc(const Allocator& a, void** p, size_t bytes);
+void dev_free(const Allocator& a, void* p);
+}  // namespace hja
+
 struct hj_grid_s {
   int device = 0;
+  hja::Allocator alloc;  // serves every device allocation of this grid
   int ndim = 0;
   int n[HJ_MAX_DIM] = {0, 0, 0, 0};
   double lo[HJ_MAX_DIM] = {0, 0, 0, 0};

@@ -13,6 +13,7 @@
 #include <dlfcn.h>
 #include <nvrtc.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -231,15 +232,18 @@ std::string group_source(const std::vector<hjd::DevGrid>& grids, const std::vect
   for (size_t c = 0; c < grids.size(); ++c) s += fixed_fn("hj_fixed_" + std::to_string(c), grids[c]);
   char buf[768];
   for (int st = 1; st <= 3; ++st) {
+    // six resident blocks of 256 threads per SM, as the single-grid stage
+    // kernels reach at 40 registers: without the bound the position switch
+    // of stage 3 takes 48 registers and only five blocks fit
     std::snprintf(buf, sizeof(buf),
-                  "extern \"C\" __global__ void __launch_bounds__(%d)\n"
+                  "extern \"C\" __global__ void __launch_bounds__(%d, %d)\n"
                   "hj_group_%d(const __grid_constant__ hjb::GroupPack pack, hjb::Ctl* ctl) {\n"
                   "  int bx, yb, slot;\n  bool check;\n"
                   "  int k = hjb::group_locate<%d>(pack, ctl, bx, yb, check, slot);\n"
                   "  if (k < 0) return;\n  unsigned r = 0u;\n"
                   "  const int q = bx * %d + (int)threadIdx.x;\n"
                   "  switch (k) {\n",
-                  threads, st, st, threads);
+                  threads, std::max(1, 1536 / threads), st, st, threads);
     s += buf;
     for (size_t c = 0; c < grids.size(); ++c) {
       std::snprintf(buf, sizeof(buf),

@@ -78,11 +78,9 @@ __device__ __forceinline__ unsigned stage_node(const DevGrid& g, const StageArgs
     if (w3 != w3) wn = w3;  // keep a NaN visible to the stop test
     a.dst[p] = wn;
     if (!check) return 0u;
-    // check 1 closes a window (the snapshot moves on); check 2 is a
-    // localized solve's mid-window look at the change since the window began
     float sv = a.snap[p];
     float r = fabsf(wn - sv);
-    if (!LOCAL || a.check != 2) a.snap[p] = wn;
+    a.snap[p] = wn;
     if (a.margin > 0) {
       // only faces of unconstrained axes: on a constrained axis the margin l
       // decides the value next to the face
@@ -167,7 +165,7 @@ __device__ __forceinline__ void flat_body(const DevGrid& g, const StageArgs& a) 
   if constexpr (STAGE == 3) {
     if (a.check) {
       if (a.slab_resid) slab_max_bits(o.slab, o.raw, a.slab_resid);
-      if (a.check != 2) block_max_bits(o.resid, a.resid);
+      block_max_bits(o.resid, a.resid);
     }
   }
 }
@@ -278,7 +276,7 @@ __device__ __forceinline__ void tile_body(const DevGrid& g, const StageArgs& a, 
   if constexpr (STAGE == 3) {
     if (a.check) {
       if (a.slab_resid) slab_max_bits(o.slab, o.raw, a.slab_resid);
-      if (a.check != 2) block_max_bits(o.resid, a.resid);
+      block_max_bits(o.resid, a.resid);
     }
   }
 }

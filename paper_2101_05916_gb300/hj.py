@@ -108,6 +108,7 @@ SIGNATURES = {
     "hj_jit_check_tiles": (_i, [_i, _P(_i), _i, _i, _i]),
     "hj_jit_check_group": (_i, [_i, _P(_i), _P(_i), _P(_i), _P(_i)]),
     "hj_set_launch_shape": (_i, [_vp, _i, _i]),
+    "hj_set_allocator": (_i, [_vp, _vp, _vp]),
     "hj_get_launch_shape": (_i, [_vp, _P(_i), _P(_i)]),
     "hj_set_value": (_i, [_vp, _vp, _i]),
     "hj_get_value": (_i, [_vp, _vp, _i]),
@@ -440,6 +441,46 @@ def hj_jit_check_group(grids) -> None:
     models = (_i * k)(*[MODELS[m] if isinstance(m, str) else int(m) for _, m, _ in grids])
     schemes = (_i * k)(*[int(s) for _, _, s in grids])
     _check(lib().hj_jit_check_group(k, nd, shapes, models, schemes))
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p)
+_allocator_keepalive = None
+
+
+def hj_set_allocator(alloc=None, free=None, user=None) -> None:
+    """hj_set_allocator with ctypes function pointers (_ALLOC_FN, _FREE_FN)
+    or None for both; the caller keeps the function objects alive."""
+    a = ctypes.cast(alloc, ctypes.c_void_p) if alloc is not None else None
+    f = ctypes.cast(free, ctypes.c_void_p) if free is not None else None
+    _check(lib().hj_set_allocator(a, f, user))
+
+
+def use_torch_allocator(on: bool = True) -> None:
+    """Route the device allocations of grids, servers and batches created
+    from now on through PyTorch's caching allocator (hj_set_allocator), so
+    that they share its pool; on=False restores cudaMalloc / cudaFree."""
+    global _allocator_keepalive
+    if not on:
+        _check(lib().hj_set_allocator(None, None, None))
+        return
+    import torch
+
+    def _alloc(nbytes, device, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), int(device))
+        except Exception:  # out of memory: the library reports HJ_ERR_OOM
+            return None
+
+    def _free(ptr, device, user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a, f = _ALLOC_FN(_alloc), _FREE_FN(_free)
+    _check(lib().hj_set_allocator(ctypes.cast(a, ctypes.c_void_p), ctypes.cast(f, ctypes.c_void_p),
+                                  None))
+    # the library keeps the function pointers; the old ones must outlive the
+    # objects created under them
+    _allocator_keepalive = (a, f, _allocator_keepalive)
 
 
 def hj_set_launch_shape(g: int, threads: int = 256, tile_rows: int = 0) -> None:

@@ -69,3 +69,16 @@ def test_default_opts(libpath):
     o = hj.hj_default_opts()
     assert o.scheme == hj.HJ_WENO5 and o.cfl == 0.5 and o.tol == 1e-4 and o.check_dt == 0.1
     assert o.use_graph == 1
+
+
+def test_allocator_hook_arguments(libpath):
+    """hj_set_allocator needs both functions or neither; no device needed."""
+    import ctypes
+    L = ctypes.CDLL(libpath)
+    L.hj_set_allocator.restype = ctypes.c_int
+    L.hj_set_allocator.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    assert L.hj_set_allocator(None, None, None) == 0
+    fn = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p)(
+        lambda n, d, u: None)
+    assert L.hj_set_allocator(ctypes.cast(fn, ctypes.c_void_p), None, None) == 1  # HJ_ERR_ARG
+    assert L.hj_set_allocator(None, None, None) == 0
