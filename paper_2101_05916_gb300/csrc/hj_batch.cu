@@ -60,13 +60,9 @@ __global__ void __launch_bounds__(kThreads) batch_stage(const __grid_constant__ 
   const Ctl& c = ctl[it.slot];
   if (!c.active) return;  // uniform: written only by the control kernel
   int lb = blockIdx.x - pack.block_begin[lo];
-  int yb = lb / it.bx;
+  int yb = it.bx >= 2 ? hjd::fast_div(lb, it.bx_m, it.bx_s) : lb;
   int bxi = lb - yb * it.bx;
-  bool check = false;
-  if (STAGE == 3) {
-    long long s1 = c.steps + 1;
-    check = (s1 % c.per == 0) || (s1 >= c.max_steps);
-  }
+  bool check = STAGE == 3 && c.check_next != 0;
   unsigned r = hjd::stage_point<D, S, M, STAGE>(it.g, it.a[STAGE - 1], bxi * kThreads + threadIdx.x,
                                                 yb, check);
   if (STAGE == 3 && check) hjd::block_max_bits(r, &ctl[it.slot].resid);
@@ -106,6 +102,7 @@ __global__ void batch_control(const int* __restrict__ slots, int nitems, Ctl* ct
     Ctl& c = ctl[slots[k]];
     if (!c.active) continue;
     long long s = ++c.steps;
+    c.check_next = ((s + 1) % c.per == 0 || s + 1 >= c.max_steps) ? 1 : 0;
     if (s % c.per == 0 || s >= c.max_steps) {
       float r = __uint_as_float(c.resid);
       c.resid = 0u;
@@ -222,6 +219,7 @@ hj_status Runner::add(hj_grid g, int mode, const hj_solve_opts& o, int* slot_out
     c.max_steps = o.max_steps > 0 ? o.max_steps : (1ll << 62);
     c.tol = o.tol;
   }
+  c.check_next = (1 % c.per == 0 || 1 >= c.max_steps) ? 1 : 0;
   host_ctl_[k] = c;
   HJ_CU(cudaMemcpyAsync(dev_ctl_ + k, &host_ctl_[k], sizeof(Ctl), cudaMemcpyHostToDevice, stream_));
   HJ_CU(cudaStreamSynchronize(stream_));
@@ -297,6 +295,7 @@ hj_status Runner::rebuild() {
     it.slot = k;
     it.bx = (it.g.plane + kThreads - 1) / kThreads;
     it.by = g->ndim == 4 ? g->n[0] : 1;
+    if (it.bx >= 2) div_consts((unsigned)it.bx, it.bx_m, it.bx_s);
     it.block_begin = gr.blocks;
     gr.pack.block_begin[gr.pack.count] = gr.blocks;
     gr.blocks += it.bx * it.by;
@@ -388,6 +387,7 @@ bool Runner::plan_group() {
     it.a[2] = hjd::StageArgs{g->B, g->W, g->W, g->snap, nullptr, dt, 0, s.clamp, s.band, s.margin};
     it.slot = k;
     it.bx = (it.g.plane + kGroupThreads - 1) / kGroupThreads;
+    if (it.bx >= 2) div_consts((unsigned)it.bx, it.bx_m, it.bx_s);
     blocks += (unsigned)it.bx * (unsigned)(it.g.ndim == 4 ? it.g.n[0] : 1);
   }
   gpack_.count = npos;

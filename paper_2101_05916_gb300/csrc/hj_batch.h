@@ -19,6 +19,8 @@ struct Item {
   int slot;             // index into the control array
   int block_begin;      // first block of this grid in the fused launch
   int bx, by;           // blocks per slab; slabs (first-axis nodes of a 4-D grid, else 1)
+  unsigned bx_m;        // bx as a multiply-shift reciprocal (bx >= 2)
+  int bx_s;
 };
 
 // Grids of one fused launch, passed as a __grid_constant__ kernel parameter.

@@ -18,6 +18,7 @@ struct Ctl {
   double tol;         // stop when the window residual drops below (negative: never)
   unsigned resid;     // running window residual (float bits)
   float last_resid;
+  int check_next;     // 1 when the next step closes a window (or reaches the cap)
 };
 
 // One position of a group launch: a grid with bx blocks of kGroupThreads
@@ -30,6 +31,8 @@ struct GroupItem {
   hjd::StageArgs a[3];  // stage 1..3 arguments (check and resid are set on the device)
   int slot;             // index into the control array
   int bx;
+  unsigned bx_m;        // bx as a multiply-shift reciprocal (hjd::fast_div), bx >= 2
+  int bx_s;
 };
 
 constexpr int kGroupItems = 16;
@@ -59,16 +62,21 @@ __device__ __forceinline__ int group_locate(const GroupPack& pack, const Ctl* ct
   slot = pack.items[lo].slot;
   const Ctl& c = ctl[slot];
   if (!c.active) return -1;
-  int per = pack.items[lo].bx;
+  const GroupItem& it = pack.items[lo];
   int lb = (int)blockIdx.x - pack.block_begin[lo];
-  yb = lb / per;
-  bx = lb - yb * per;
-  check = false;
-  if (STAGE == 3) {
-    long long s1 = c.steps + 1;
-    check = (s1 % c.per == 0) || (s1 >= c.max_steps);
-  }
+  yb = it.bx >= 2 ? hjd::fast_div(lb, it.bx_m, it.bx_s) : lb;
+  bx = lb - yb * it.bx;
+  check = STAGE == 3 && c.check_next != 0;
   return lo;
+}
+
+// Multiply-shift reciprocal (m, s) of a divisor d >= 2 for hjd::fast_div.
+__host__ __device__ inline void div_consts(unsigned d, unsigned& m, int& s) {
+  int l = 0;
+  while ((1ull << l) < d) ++l;
+  unsigned long long num = 1ull << (31 + l);
+  m = (unsigned)((num + d - 1) / d);
+  s = l - 1;
 }
 
 }  // namespace hjb
