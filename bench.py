@@ -104,6 +104,8 @@ def parse():
                     help="run only this many fixed TVD-RK3 steps on one grid (for ncu)")
     ap.add_argument("--profile-n", type=int, default=N_FINE,
                     help="nodes per axis of the 4-D grid of --profile-steps")
+    ap.add_argument("--profile-tile", type=int, default=0,
+                    help="row tiles of this many lines in --profile-steps (0: the flat mapping)")
     return ap.parse_args()
 
 
@@ -417,11 +419,14 @@ def profile_only(args, hj, wl):
     import torch
     spec = wl.quad_x4(args.profile_n, BOUND)
     g = hj.Grid.from_spec(spec, stream=torch.cuda.current_stream())
+    if args.profile_tile:
+        g.set_launch_shape(256, args.profile_tile)
     g.solve(hj.HJ_COLD, scheme=5, fixed_steps=1, clamp=CLAMP)
     hj.hj_jit_wait()
     st = g.solve(hj.HJ_COLD, scheme=5, fixed_steps=args.profile_steps, clamp=CLAMP)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_steps": st["steps"], "dt": st["dt"], "n": args.profile_n}))
+    print(json.dumps({"profile_steps": st["steps"], "dt": st["dt"], "n": args.profile_n,
+                      "launch_shape": g.launch_shape()}))
     g.close()
 
 

@@ -298,18 +298,23 @@ __device__ __forceinline__ void load_line(const float* __restrict__ src, int p, 
   }
 }
 
-// The same line along the fastest axis (stride 1), without branches.  The
-// 2R+1 values are loaded unclamped at immediate offsets.  Near a row end some
+// The same line along the fastest axis (stride 1).  The 2R+1 values are
+// loaded unclamped at immediate offsets.  Near a row end some
 // of them come from the neighbouring row, or from the guard floats every
 // field carries before its first and after its last node.  Those slots are
-// then replaced, with selects, by the linear continuation of the row through
-// its two outermost nodes.  Nearly every warp holds a lane within R nodes of
-// a row end, so a branch here would run both paths in almost every warp.
+// then replaced, with selects rather than a per-lane branch (a warp of a
+// short-line grid nearly always holds a lane within R nodes of a row end),
+// by the linear continuation of the row through its two outermost nodes.
 template <int R>
 __device__ __forceinline__ void load_fast_line(const float* __restrict__ src, int p, int i, int n,
                                                float (&v)[2 * R + 1]) {
 #pragma unroll
   for (int k = -R; k <= R; ++k) v[k + R] = __ldg(src + p + k);
+  // Only a warp that holds a node within R of a line end needs the ghost
+  // values; the others (about half the warps at 81 nodes per line) skip
+  // the row-end loads and selects.  The vote runs over the lanes still
+  // active here, which is warp-uniform in outcome.
+  if (!__any_sync(__activemask(), i < R || i > n - 1 - R)) return;
   const float* row = src + (p - i);
   float w0 = __ldg(row), w1 = __ldg(row + 1);
   float wn = __ldg(row + (n - 1)), wm = __ldg(row + (n - 2));

@@ -24,8 +24,11 @@ struct Ctl {
 // One position of a group launch: a grid with bx blocks of kGroupThreads
 // nodes per slab of the flat mapping (slabs: the first axis of a 4-D grid,
 // else one).  The group kernel holds one body per position, compiled for
-// that grid's kind, shape and model constants.  A position without a grid
-// has bx = 0 (no blocks).
+// that grid's kind, shape and model constants; a block finds its position
+// by comparing its index with the positions' first blocks, and each body
+// reads its position's fields with literal indices (constant-bank operands,
+// as in the single-grid kernel).  A position without a grid has no blocks:
+// its first block equals its successor's.
 struct GroupItem {
   hjd::DevGrid g;
   hjd::StageArgs a[3];  // stage 1..3 arguments (check and resid are set on the device)
@@ -42,33 +45,6 @@ struct GroupPack {
   int block_begin[kGroupItems + 1];
   GroupItem items[kGroupItems];
 };
-
-// The block's position in a group launch: its index k (binary search over
-// the block offsets; positions without blocks are never found), its block
-// (bx, yb) in that grid's flat mapping, its control slot, and whether this
-// stage-3 launch closes the grid's window.  -1 when the grid no longer
-// steps (the whole block returns).  The kernel then reads the descriptor
-// and stage arguments of position k with a literal index, so that they
-// stay constant-bank operands as in the single-grid kernel.
-template <int STAGE>
-__device__ __forceinline__ int group_locate(const GroupPack& pack, const Ctl* ctl, int& bx,
-                                            int& yb, bool& check, int& slot) {
-  int lo = 0, hi = pack.count - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (pack.block_begin[mid] <= (int)blockIdx.x) lo = mid;
-    else hi = mid - 1;
-  }
-  slot = pack.items[lo].slot;
-  const Ctl& c = ctl[slot];
-  if (!c.active) return -1;
-  const GroupItem& it = pack.items[lo];
-  int lb = (int)blockIdx.x - pack.block_begin[lo];
-  yb = it.bx >= 2 ? hjd::fast_div(lb, it.bx_m, it.bx_s) : lb;
-  bx = lb - yb * it.bx;
-  check = STAGE == 3 && c.check_next != 0;
-  return lo;
-}
 
 // Multiply-shift reciprocal (m, s) of a divisor d >= 2 for hjd::fast_div.
 __host__ __device__ inline void div_consts(unsigned d, unsigned& m, int& s) {

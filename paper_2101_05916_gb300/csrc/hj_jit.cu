@@ -230,7 +230,8 @@ std::string group_source(const std::vector<hjd::DevGrid>& grids, const std::vect
                          int threads) {
   std::string s = "#include \"hj_group.cuh\"\n";
   for (size_t c = 0; c < grids.size(); ++c) s += fixed_fn("hj_fixed_" + std::to_string(c), grids[c]);
-  char buf[768];
+  char buf[1024];
+  const int npos = (int)grids.size();
   for (int st = 1; st <= 3; ++st) {
     // six resident blocks of 256 threads per SM, as the single-grid stage
     // kernels reach at 40 registers: without the bound the position switch
@@ -238,27 +239,40 @@ std::string group_source(const std::vector<hjd::DevGrid>& grids, const std::vect
     std::snprintf(buf, sizeof(buf),
                   "extern \"C\" __global__ void __launch_bounds__(%d, %d)\n"
                   "hj_group_%d(const __grid_constant__ hjb::GroupPack pack, hjb::Ctl* ctl) {\n"
-                  "  int bx, yb, slot;\n  bool check;\n"
-                  "  int k = hjb::group_locate<%d>(pack, ctl, bx, yb, check, slot);\n"
-                  "  if (k < 0) return;\n  unsigned r = 0u;\n"
-                  "  const int q = bx * %d + (int)threadIdx.x;\n"
-                  "  switch (k) {\n",
-                  threads, std::max(1, 1536 / threads), st, st, threads);
+                  "  const int b = (int)blockIdx.x;\n  int k = 0;\n",
+                  threads, std::max(1, 1536 / threads), st);
     s += buf;
-    for (size_t c = 0; c < grids.size(); ++c) {
-      std::snprintf(buf, sizeof(buf),
-                    "    case %d: {\n"
-                    "      hjd::StageArgs a = pack.items[%d].a[%d];\n"
-                    "      a.check = check ? 1 : 0;\n      a.resid = &ctl[slot].resid;\n"
-                    "      r = hjd::stage_point<%d, %d, %d, %d>(hj_fixed_%d(pack.items[%d].g),"
-                    " a, q, yb, check);\n      break;\n    }\n",
-                    (int)c, (int)c, st - 1, grids[c].ndim, schemes[c], grids[c].model, st, (int)c,
-                    (int)c);
+    // the block's position: the last one whose first block is not after it
+    // (positions without blocks share their successor's first block)
+    for (int c = 1; c < npos; ++c) {
+      std::snprintf(buf, sizeof(buf), "  if (b >= pack.block_begin[%d]) k = %d;\n", c, c);
       s += buf;
     }
-    s += "  }\n";
-    s += st == 3 ? "  if (check) hjd::block_max_bits(r, &ctl[slot].resid);\n}\n"
-                 : "  (void)r;\n}\n";
+    s += "  switch (k) {\n";
+    for (int c = 0; c < npos; ++c) {
+      std::snprintf(buf, sizeof(buf),
+                    "    case %d: {\n"
+                    "      const int slot = pack.items[%d].slot;\n"
+                    "      if (!ctl[slot].active) return;\n"
+                    "      const int lb = b - pack.block_begin[%d];\n"
+                    "      const int yb = pack.items[%d].bx >= 2 ? hjd::fast_div(lb, pack.items[%d].bx_m,"
+                    " pack.items[%d].bx_s) : lb;\n"
+                    "      const int bx = lb - yb * pack.items[%d].bx;\n"
+                    "      const bool check = %s;\n"
+                    "      hjd::StageArgs a = pack.items[%d].a[%d];\n"
+                    "      a.check = check ? 1 : 0;\n      a.resid = &ctl[slot].resid;\n",
+                    c, c, c, c, c, c, c, st == 3 ? "ctl[slot].check_next != 0" : "false", c,
+                    st - 1);
+      s += buf;
+      std::snprintf(buf, sizeof(buf),
+                    "      unsigned r = hjd::stage_point<%d, %d, %d, %d>(hj_fixed_%d(pack.items[%d].g),"
+                    " a, bx * %d + (int)threadIdx.x, yb, check);\n"
+                    "      %s\n      return;\n    }\n",
+                    grids[c].ndim, schemes[c], grids[c].model, st, c, c, threads,
+                    st == 3 ? "if (check) hjd::block_max_bits(r, a.resid);" : "(void)r;");
+      s += buf;
+    }
+    s += "  }\n}\n";
   }
   return s;
 }
