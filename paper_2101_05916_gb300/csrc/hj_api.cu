@@ -90,12 +90,7 @@ hjd::DevGrid devgrid(const hj_grid g) {
   // multiply-shift reciprocals of the three fastest axis lengths (see fast_div)
   for (int k = 0; k < 3; ++k) {
     int ax = g->ndim - 1 - k;
-    unsigned dv = ax >= 0 ? (unsigned)g->n[ax] : 2u;
-    int l = 0;
-    while ((1ull << l) < dv) ++l;
-    unsigned long long num = 1ull << (31 + l);
-    d.div_m[k] = (unsigned)((num + dv - 1) / dv);
-    d.div_s[k] = l - 1;
+    hjd::div_consts(ax >= 0 ? (unsigned)g->n[ax] : 2u, d.div_m[k], d.div_s[k]);
   }
   for (int i = 0; i < g->ndim; ++i) {
     d.lo[i] = (float)g->lo[i];

@@ -295,7 +295,7 @@ hj_status Runner::rebuild() {
     it.slot = k;
     it.bx = (it.g.plane + kThreads - 1) / kThreads;
     it.by = g->ndim == 4 ? g->n[0] : 1;
-    if (it.bx >= 2) div_consts((unsigned)it.bx, it.bx_m, it.bx_s);
+    if (it.bx >= 2) hjd::div_consts((unsigned)it.bx, it.bx_m, it.bx_s);
     it.block_begin = gr.blocks;
     gr.pack.block_begin[gr.pack.count] = gr.blocks;
     gr.blocks += it.bx * it.by;
@@ -387,7 +387,7 @@ bool Runner::plan_group() {
     it.a[2] = hjd::StageArgs{g->B, g->W, g->W, g->snap, nullptr, dt, 0, s.clamp, s.band, s.margin};
     it.slot = k;
     it.bx = (it.g.plane + kGroupThreads - 1) / kGroupThreads;
-    if (it.bx >= 2) div_consts((unsigned)it.bx, it.bx_m, it.bx_s);
+    if (it.bx >= 2) hjd::div_consts((unsigned)it.bx, it.bx_m, it.bx_s);
     blocks += (unsigned)it.bx * (unsigned)(it.g.ndim == 4 ? it.g.n[0] : 1);
   }
   gpack_.count = npos;

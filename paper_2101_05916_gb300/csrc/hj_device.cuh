@@ -108,6 +108,15 @@ __device__ __forceinline__ int fast_div(int q, unsigned m, int s) {
   return (int)(__umulhi((unsigned)q, m) >> s);
 }
 
+// The (m, s) of a divisor d >= 2 for fast_div.
+__host__ __device__ inline void div_consts(unsigned d, unsigned& m, int& s) {
+  int l = 0;
+  while ((1ull << l) < d) ++l;
+  unsigned long long num = 1ull << (31 + l);
+  m = (unsigned)((num + d - 1) / d);
+  s = l - 1;
+}
+
 // ---------------------------------------------------------------- geometry
 
 // Margin l = -c to the constraint set at node p, coordinates x: distance to

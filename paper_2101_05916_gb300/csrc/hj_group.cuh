@@ -1,6 +1,6 @@
 // hj_group.cuh -- device-side structures of batched stepping: the per-grid
 // control state, and the pack of a group launch (one launch per RK stage
-// over the row tiles of every active grid of a batch, whatever its kind).
+// over the blocks of every active grid of a batch, whatever its kind).
 #pragma once
 
 #include "hj_stage.cuh"
@@ -45,14 +45,5 @@ struct GroupPack {
   int block_begin[kGroupItems + 1];
   GroupItem items[kGroupItems];
 };
-
-// Multiply-shift reciprocal (m, s) of a divisor d >= 2 for hjd::fast_div.
-__host__ __device__ inline void div_consts(unsigned d, unsigned& m, int& s) {
-  int l = 0;
-  while ((1ull << l) < d) ++l;
-  unsigned long long num = 1ull << (31 + l);
-  m = (unsigned)((num + d - 1) / d);
-  s = l - 1;
-}
 
 }  // namespace hjb
