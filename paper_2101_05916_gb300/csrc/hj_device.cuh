@@ -271,12 +271,49 @@ __device__ __forceinline__ double node_diff2(const DevGrid& g, const float* W, i
 
 // ---------------------------------------------------------- grid lines
 
-// The 2R+1 values of the grid line through node p along one axis; ghost
-// nodes beyond either end continue the line linearly through its two
-// outermost nodes.
+// A grid line around node i (of n along one axis) is handled as its 2R
+// first differences Dk[k] = W(i + k - R + 1) - W(i + k - R), k = 0 .. 2R-1.
+// Ghost nodes beyond either end continue the line linearly through its two
+// outermost nodes, so every difference that reaches past an end equals the
+// line's edge difference there: W(1) - W(0) at the start, W(n-1) - W(n-2)
+// at the end.
+//
+// edge_diffs applies that rule to differences that are right wherever both
+// nodes of a slot lie on the line (whatever they hold elsewhere).  The
+// start's edge difference sits in slot R - i when i < R, the end's in slot
+// R - 1 + (n-1-i) when n-1-i < R; both are read before any slot is
+// replaced.  Selects, not branches: lanes away from the ends keep every
+// slot.  n >= 2 keeps the two replaced ranges apart.
 template <int R>
-__device__ __forceinline__ void load_line(const float* __restrict__ src, int p, int stride, int i,
-                                          int n, float (&v)[2 * R + 1]) {
+__device__ __forceinline__ void edge_diffs(float (&Dk)[2 * R], int i, int n) {
+  const int r = n - 1 - i;
+  float dl = Dk[R], dr = Dk[R - 1];
+#pragma unroll
+  for (int j = 1; j < R; ++j) {
+    dl = (i == j) ? Dk[R - j] : dl;
+    dr = (r == j) ? Dk[R - 1 + j] : dr;
+  }
+#pragma unroll
+  for (int k = 0; k < R; ++k) Dk[k] = (k + i < R) ? dl : Dk[k];
+#pragma unroll
+  for (int k = R; k < 2 * R; ++k) Dk[k] = (k - r >= R) ? dr : Dk[k];
+}
+
+template <int R>
+__device__ __forceinline__ void diffs_of(const float (&v)[2 * R + 1], float (&Dk)[2 * R]) {
+#pragma unroll
+  for (int k = 0; k < 2 * R; ++k) Dk[k] = v[k + 1] - v[k];
+}
+
+// The differences of the line through node p along an axis of stride
+// `stride` (a slower axis).  Nodes R or more from both ends load their
+// 2R+1 values at offsets that are the same for the whole warp; the others
+// load with the index clamped to the line (so every address stays inside
+// the field) and replace the differences past an end.
+template <int R>
+__device__ __forceinline__ void line_diffs(const float* __restrict__ src, int p, int stride, int i,
+                                           int n, float (&Dk)[2 * R]) {
+  float v[2 * R + 1];
   if (i >= R && i < n - R) {
     // one per-thread base address plus offsets that are the same for the
     // whole warp: 64-bit integer adds instead of a multiply-add per load
@@ -284,6 +321,7 @@ __device__ __forceinline__ void load_line(const float* __restrict__ src, int p, 
     const long long sb = (long long)stride * (long long)sizeof(float);
 #pragma unroll
     for (int k = -R; k <= R; ++k) v[k + R] = __ldg(reinterpret_cast<const float*>(c + k * sb));
+    diffs_of<R>(v, Dk);
     return;
   }
 #pragma unroll
@@ -291,54 +329,25 @@ __device__ __forceinline__ void load_line(const float* __restrict__ src, int p, 
     int j = min(max(i + k, 0), n - 1);
     v[k + R] = __ldg(src + p + (j - i) * stride);
   }
-  if (i < R) {
-    float w0 = __ldg(src + p - i * stride);
-    float s = w0 - __ldg(src + p + (1 - i) * stride);
-#pragma unroll
-    for (int k = -R; k <= R; ++k)
-      if (i + k < 0) v[k + R] = fmaf((float)(-(i + k)), s, w0);
-  }
-  if (i > n - 1 - R) {
-    float wn = __ldg(src + p + (n - 1 - i) * stride);
-    float s = wn - __ldg(src + p + (n - 2 - i) * stride);
-#pragma unroll
-    for (int k = -R; k <= R; ++k)
-      if (i + k > n - 1) v[k + R] = fmaf((float)(i + k - (n - 1)), s, wn);
-  }
+  diffs_of<R>(v, Dk);
+  edge_diffs<R>(Dk, i, n);
 }
 
-// The same line along the fastest axis (stride 1).  The 2R+1 values are
-// loaded unclamped at immediate offsets.  Near a row end some
-// of them come from the neighbouring row, or from the guard floats every
-// field carries before its first and after its last node.  Those slots are
-// then replaced, with selects rather than a per-lane branch (a warp of a
-// short-line grid nearly always holds a lane within R nodes of a row end),
-// by the linear continuation of the row through its two outermost nodes.
+// The same along the fastest axis (stride 1), from the 2R+1 line values v
+// around the node: loaded unclamped at immediate offsets by the caller
+// (near a row end some of them come from the neighbouring row, or from the
+// guard floats every field carries before its first and after its last
+// node), or read from a shared-memory copy of the row.  Returns the node's
+// own value.  Only a warp that holds a node within R of a line end applies
+// the end rule; the others (about half the warps at 81 nodes per line)
+// skip it.  The vote runs over the lanes still active here, which is
+// warp-uniform in outcome.
 template <int R>
-__device__ __forceinline__ void load_fast_line(const float* __restrict__ src, int p, int i, int n,
-                                               float (&v)[2 * R + 1]) {
-#pragma unroll
-  for (int k = -R; k <= R; ++k) v[k + R] = __ldg(src + p + k);
-  // Only a warp that holds a node within R of a line end needs the ghost
-  // values; the others (about half the warps at 81 nodes per line) skip
-  // the row-end loads and selects.  The vote runs over the lanes still
-  // active here, which is warp-uniform in outcome.
-  if (!__any_sync(__activemask(), i < R || i > n - 1 - R)) return;
-  const float* row = src + (p - i);
-  float w0 = __ldg(row), w1 = __ldg(row + 1);
-  float wn = __ldg(row + (n - 1)), wm = __ldg(row + (n - 2));
-  float slo = w0 - w1, shi = wn - wm;
-  float fi = (float)i, fr = (float)(n - 1 - i);
-#pragma unroll
-  for (int k = 0; k < R; ++k) {
-    float e = (float)(R - k) - fi;  // ghost depth below node 0 (<= 0: a real node)
-    v[k] = (e > 0.f) ? fmaf(e, slo, w0) : v[k];
-  }
-#pragma unroll
-  for (int k = R + 1; k <= 2 * R; ++k) {
-    float e = (float)(k - R) - fr;  // ghost depth beyond node n-1
-    v[k] = (e > 0.f) ? fmaf(e, shi, wn) : v[k];
-  }
+__device__ __forceinline__ float fast_line_diffs(const float (&v)[2 * R + 1], int i, int n,
+                                                 float (&Dk)[2 * R]) {
+  diffs_of<R>(v, Dk);
+  if (__any_sync(__activemask(), i < R || i > n - 1 - R)) edge_diffs<R>(Dk, i, n);
+  return v[R];
 }
 
 // ------------------------------------------------------------- slopes
@@ -360,6 +369,15 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 // differences, so both run as the two lanes of packed FP32 pairs: lane x
 // holds the left side's operand, lane y the right side's.  Packed pairs
 // halve the issue slots of the arithmetic.
+//
+// Lane y runs on its second differences with the sign flipped.  Mirrored,
+// they are (D4 - D5, D3 - D4, D2 - D3, D1 - D2); flipped, the two lanes share
+// the five second differences of the line (D1 - D0 .. D5 - D4), and C is one
+// value in both lanes.  The indicators are even in them and the candidate
+// offsets odd, and rounding to nearest is symmetric in sign, so lane y ends
+// with exactly the negated offset N / M: its X2 slot holds -D3 and the
+// result is negated once more.  The slopes are bit for bit those of the
+// unflipped form.
 //
 // The arithmetic is the textbook scheme, rewritten in the second
 // differences A, B, C, E of the five upwind differences X0..X4 (A = X1 - X0,
@@ -387,9 +405,10 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 //     It takes one reciprocal per side.
 __device__ __forceinline__ void weno5_pair(float D0, float D1, float D2, float D3, float D4,
                                            float D5, float floor_, float& pm_h, float& pp_h) {
-  const float2 A = make_float2(D1 - D0, D4 - D5), B = make_float2(D2 - D1, D3 - D4);
-  const float2 C = make_float2(D3 - D2, D2 - D3), E = make_float2(D4 - D3, D1 - D2);
-  const float2 X2 = make_float2(D2, D3);
+  const float a = D1 - D0, b = D2 - D1, c = D3 - D2, d = D4 - D3, f = D5 - D4;
+  const float2 A = make_float2(a, f), B = make_float2(b, d);
+  const float2 C = make_float2(c, c), E = make_float2(d, b);
+  const float2 X2 = make_float2(D2, -D3);
   const float2 k = f2s(39.f / 64.f);
   float2 kB2 = mul2(mul2(k, B), B);
   float2 kC2 = mul2(mul2(k, C), C);
@@ -416,41 +435,44 @@ __device__ __forceinline__ void weno5_pair(float D0, float D1, float D2, float D
   float2 den = fma2(f2s(1.2f), Q1, fma2(f2s(3.f), Q2, mul2(f2s(1.5f), Q3)));
   float2 w = fma2(num, make_float2(rcp_approx(den.x), rcp_approx(den.y)), X2);
   pm_h = w.x;
-  pp_h = w.y;
+  pp_h = -w.y;
 }
 
-// Per scheme: the stencil radius R and raw one-sided slopes whose scale the
-// caller removes with folded per-axis constants (half and half-alpha times
-// 1/h for first order and ENO2, times 1/(6h) for WENO5).
+// Per scheme: the stencil radius R and raw one-sided slopes, from the 2R
+// first differences Dk of the node's line (Dk[k] spans offsets k-R and
+// k-R+1), whose scale the caller removes with folded per-axis constants
+// (half and half-alpha times 1/h for first order and ENO2, times 1/(6h) for
+// WENO5).
 template <int S>
 struct Slopes;
 
 template <>
 struct Slopes<1> {
   static constexpr int R = 1;
-  __device__ __forceinline__ static void eval(const float (&v)[3], const DevGrid&, int,
+  __device__ __forceinline__ static void eval(const float (&Dk)[2], const DevGrid&, int,
                                               float& pm, float& pp) {
-    pm = v[1] - v[0];
-    pp = v[2] - v[1];
+    pm = Dk[0];
+    pp = Dk[1];
   }
   __device__ __forceinline__ static float half(const DevGrid& g, int d) { return g.hih[d]; }
   __device__ __forceinline__ static float half_alpha(const DevGrid& g, int d) { return g.haih[d]; }
 };
 
 // ENO2: first difference plus half the smaller (in magnitude) of the two
-// adjacent second differences; ties take the left one.
+// adjacent second differences; ties take the left one.  The second
+// differences are differences of the first ones.
 template <>
 struct Slopes<2> {
   static constexpr int R = 2;
-  __device__ __forceinline__ static void eval(const float (&v)[5], const DevGrid&, int,
+  __device__ __forceinline__ static void eval(const float (&Dk)[4], const DevGrid&, int,
                                               float& pm, float& pp) {
-    float a = fmaf(-2.f, v[1], v[2] + v[0]);
-    float b = fmaf(-2.f, v[2], v[3] + v[1]);
-    float c = fmaf(-2.f, v[3], v[4] + v[2]);
+    float a = Dk[1] - Dk[0];
+    float b = Dk[2] - Dk[1];
+    float c = Dk[3] - Dk[2];
     float m1 = (fabsf(a) <= fabsf(b)) ? a : b;
     float m2 = (fabsf(b) <= fabsf(c)) ? b : c;
-    pm = fmaf(0.5f, m1, v[2] - v[1]);
-    pp = fmaf(-0.5f, m2, v[3] - v[2]);
+    pm = fmaf(0.5f, m1, Dk[1]);
+    pp = fmaf(-0.5f, m2, Dk[2]);
   }
   __device__ __forceinline__ static float half(const DevGrid& g, int d) { return g.hih[d]; }
   __device__ __forceinline__ static float half_alpha(const DevGrid& g, int d) { return g.haih[d]; }
@@ -459,22 +481,21 @@ struct Slopes<2> {
 template <>
 struct Slopes<5> {
   static constexpr int R = 3;
-  __device__ __forceinline__ static void eval(const float (&v)[7], const DevGrid& g, int d,
+  __device__ __forceinline__ static void eval(const float (&Dk)[6], const DevGrid& g, int d,
                                               float& pm, float& pp) {
-    weno5_pair(v[1] - v[0], v[2] - v[1], v[3] - v[2], v[4] - v[3], v[5] - v[4], v[6] - v[5],
-               g.wfloor[d], pm, pp);
+    weno5_pair(Dk[0], Dk[1], Dk[2], Dk[3], Dk[4], Dk[5], g.wfloor[d], pm, pp);
   }
   __device__ __forceinline__ static float half(const DevGrid& g, int d) { return g.hih[d]; }
   __device__ __forceinline__ static float half_alpha(const DevGrid& g, int d) { return g.haih[d]; }
 };
 
 // L(src) at node p with multi-index idx; also returns src[p] in `center`.
-// The last axis is the fastest (stride 1).  Its line comes either from
-// `fast`, a shared-memory copy of the node's row with its ghost values
-// already in place (fast[k] is the line value at offset k, k = -R..R), or,
-// when fast is null, from global memory branch-free at immediate offsets
-// (load_fast_line); src then needs at least 3 readable guard floats before
-// its first and after its last node.  Both give the same values.
+// The last axis is the fastest (stride 1).  Its line values come either
+// from `fast`, a shared-memory copy of the node's row (fast[k] is the line
+// value at offset k, k = -R..R), or, when fast is null, from global memory
+// at immediate offsets; src then needs at least 3 readable guard floats
+// before its first and after its last node.  Both give the same
+// differences (fast_line_diffs).
 template <int D, int S, int M>
 __device__ __forceinline__ float lf_rhs(const DevGrid& g, const float* __restrict__ src, int p,
                                         const int (&idx)[D], const float (&x)[D], float& center,
@@ -484,20 +505,17 @@ __device__ __forceinline__ float lf_rhs(const DevGrid& g, const float* __restric
   float diss = 0.f;
 #pragma unroll
   for (int d = 0; d < D; ++d) {
-    float v[2 * R + 1];
+    float Dk[2 * R];
     if (d == D - 1) {
-      if (fast) {
+      float v[2 * R + 1];
 #pragma unroll
-        for (int k = -R; k <= R; ++k) v[k + R] = fast[k];
-      } else {
-        load_fast_line<R>(src, p, idx[d], g.n[d], v);
-      }
+      for (int k = -R; k <= R; ++k) v[k + R] = fast ? fast[k] : __ldg(src + p + k);
+      center = fast_line_diffs<R>(v, idx[d], g.n[d], Dk);
     } else {
-      load_line<R>(src, p, g.stride[d], idx[d], g.n[d], v);
+      line_diffs<R>(src, p, g.stride[d], idx[d], g.n[d], Dk);
     }
-    if (d == D - 1) center = v[R];
     float pm, pp;
-    Slopes<S>::eval(v, g, d, pm, pp);
+    Slopes<S>::eval(Dk, g, d, pm, pp);
     pbar[d] = Slopes<S>::half(g, d) * (pm + pp);
     diss = fmaf(Slopes<S>::half_alpha(g, d), pp - pm, diss);
   }

@@ -208,11 +208,13 @@ std::string source(const hjd::DevGrid& g, int scheme, int threads, bool local) {
     }
     return s;
   }
+  // 2048 threads per SM: 32 registers per thread, which the folded kernels
+  // fit without spills (40 registers and 1536 threads otherwise)
   for (int st = 1; st <= 3; ++st) {
     std::snprintf(buf, sizeof(buf),
-                  "extern \"C\" __global__ void __launch_bounds__(%d)\n"
+                  "extern \"C\" __global__ void __launch_bounds__(%d, %d)\n"
                   "hj_stage_%d(const hjd::DevGrid g, const hjd::StageArgs a) {\n",
-                  threads, st);
+                  threads, 2048 / threads, st);
     s += buf;
     std::snprintf(buf, sizeof(buf), "  hjd::flat_body<%d, %d, %d, %d, %s>(hj_fixed(g), a);\n}\n",
                   g.ndim, scheme, g.model, st, local ? "true" : "false");
@@ -233,14 +235,13 @@ std::string group_source(const std::vector<hjd::DevGrid>& grids, const std::vect
   char buf[1024];
   const int npos = (int)grids.size();
   for (int st = 1; st <= 3; ++st) {
-    // six resident blocks of 256 threads per SM, as the single-grid stage
-    // kernels reach at 40 registers: without the bound the position switch
-    // of stage 3 takes 48 registers and only five blocks fit
+    // 2048 threads per SM at 32 registers, as the single-grid stage kernels
+    // (without the bound the position switch of stage 3 takes 48 registers)
     std::snprintf(buf, sizeof(buf),
                   "extern \"C\" __global__ void __launch_bounds__(%d, %d)\n"
                   "hj_group_%d(const __grid_constant__ hjb::GroupPack pack, hjb::Ctl* ctl) {\n"
                   "  const int b = (int)blockIdx.x;\n  int k = 0;\n",
-                  threads, std::max(1, 1536 / threads), st);
+                  threads, std::max(1, 2048 / threads), st);
     s += buf;
     // the block's position: the last one whose first block is not after it
     // (positions without blocks share their successor's first block)
