@@ -298,7 +298,9 @@ hj_status hj_alpha(hj_grid g, double* alpha_out);
  *     interval of the prior inside the new one, and the prior's constraint
  *     box containing the new one, and the VI clamp: under HJ_CLAMP_MONOTONE
  *     the solve's limit depends on its start, so such a request always
- *     solves cold.  Otherwise the request solves cold.
+ *     solves cold.  Otherwise the request solves cold.  Priors whose box
+ *     contains the new one only once moved are used only after
+ *     hj_server_set_translated_starts(s, 1).
  *   - Memory: results stay on the device until hj_server_release.  Released
  *     results that are still a key's resident prior are evicted (least
  *     recently used first) when the budget is needed.
@@ -386,6 +388,19 @@ hj_status hj_server_get_stats(hj_server s, hj_server_stats* out);
  * Applies from the next admission on. */
 enum { HJ_ORDER_FIFO = 0, HJ_ORDER_SHORTEST = 1 };
 hj_status hj_server_set_policy(hj_server s, int order, long long max_active_nodes);
+
+/* Warm starts from translated priors (Sec. III-B reuse of a prior whose
+ * constraint box moved along the position axis; see hj_translate).
+ *   enable = 1: a HJ_WARM request whose key's prior dominates only once its
+ *     box is moved warm-starts from the moved prior (counted in
+ *     translated_starts).
+ *   enable = 0 (the default): such a request solves cold.
+ * The schemes here are not monotone, so a solve's limit can depend on its
+ * start: on the 2-D ENO2 requests of the seeded serving trace a translated
+ * start landed 1e-5 to 1e-4 (relative) above the cold fixed point at every
+ * stop tolerance tried, and saved no steps in four of five cases.
+ * HJ_ERR_ARG: enable not 0 or 1.  Applies from the next admission on. */
+hj_status hj_server_set_translated_starts(hj_server s, int enable);
 
 /* Safety filter of the safe-learning loop (Sec. II-B, II-C) for a system
  * decomposed into independent subsystem grids (Sec. III-A, e.g. the 10-D

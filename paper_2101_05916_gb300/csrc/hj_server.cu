@@ -174,6 +174,7 @@ struct hj_server_s {
   size_t used = 0;
   int order = HJ_ORDER_FIFO;
   long long max_active_nodes = 0;
+  bool translated_starts = false;  // warm starts from translated priors (opt-in)
   long long active_nodes = 0;
   hj_server_stats st{};
   std::vector<double> latencies;
@@ -305,7 +306,7 @@ void hj_server_s::admit_locked(std::vector<long long>& admitted) {
             mode = HJ_WARM;
             p.last_use = Clock::now();
           }
-        } else if (p.g && dominates_translated(p.r, q.r, shift)) {
+        } else if (translated_starts && p.g && dominates_translated(p.r, q.r, shift)) {
           if (hj_translate(p.g, g, shift) == HJ_OK) {
             mode = HJ_WARM;
             st.translated_starts++;
@@ -683,6 +684,14 @@ hj_status hj_server_set_policy(hj_server s, int order, long long max_active_node
   s->order = order;
   s->max_active_nodes = max_active_nodes;
   s->cv_work.notify_all();
+  return HJ_OK;
+}
+
+hj_status hj_server_set_translated_starts(hj_server s, int enable) {
+  if (!s) return hja::fail(HJ_ERR_ARG, "NULL server");
+  if (enable != 0 && enable != 1) return hja::fail(HJ_ERR_ARG, "enable must be 0 or 1");
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->translated_starts = enable != 0;
   return HJ_OK;
 }
 

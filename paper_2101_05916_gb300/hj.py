@@ -131,6 +131,7 @@ SIGNATURES = {
     "hj_server_cancel": (_i, [_vp, _ll]),
     "hj_server_get_stats": (_i, [_vp, _P(hj_server_stats)]),
     "hj_server_set_policy": (_i, [_vp, _i, _ll]),
+    "hj_server_set_translated_starts": (_i, [_vp, _i]),
     "hj_solve_fixed_static": (_i, [_i, _P(_i), _P(_d), _P(_d), _i, _P(_d), _i, _P(_d), _P(_d),
                                    _i, _P(_d), _P(_d), _i, _i, _d, _ll, _i, _vp, _vp]),
 }
@@ -664,6 +665,10 @@ def hj_server_cancel(s: int, ticket: int) -> None:
 
 def hj_server_set_policy(s: int, order: int = HJ_ORDER_FIFO, max_active_nodes: int = 0) -> None:
     _check(lib().hj_server_set_policy(s, int(order), int(max_active_nodes)))
+
+
+def hj_server_set_translated_starts(s: int, enable: bool) -> None:
+    _check(lib().hj_server_set_translated_starts(s, 1 if enable else 0))
 
 
 def hj_server_get_stats(s: int) -> Dict:

@@ -265,11 +265,13 @@ def test_monotone_clamp_requests_never_warm_start(hj):
 
 
 def test_translated_prior_warm_start(hj):
-    """A key's resident prior whose constraint box, moved along the position
-    axis, equals the new one warm-starts the request through hj_translate and
-    reaches the cold fixed point; a moved box with a smaller wind bound does
-    not dominate and starts cold."""
+    """With translated starts enabled, a key's resident prior whose
+    constraint box, moved along the position axis, equals the new one
+    warm-starts the request through hj_translate and reaches the cold fixed
+    point; a moved box with a smaller wind bound does not dominate and starts
+    cold."""
     s = hj.hj_server_create(4 << 30, 8)
+    hj.hj_server_set_translated_starts(s, True)
     key = 91
     first = wl.quad_z(101, 0.5, (0.5, 2.5))
     rc, st0, _ = fetch(hj, s, run(hj, s, first, 2, 0.0, hj.HJ_WARM, key, tol=1e-5), first)
@@ -289,6 +291,31 @@ def test_translated_prior_warm_start(hj):
     g.close()
     assert st1["steps"] < stc["steps"]
     assert np.abs(W - Wc).max() <= REL * np.abs(Wc).max()
+
+
+def test_translated_starts_are_off_by_default(hj):
+    """Without hj_server_set_translated_starts a moved-box prior is not used:
+    the request solves cold and its result is its own cold solve bit for
+    bit; the setting takes only 0 or 1."""
+    s = hj.hj_server_create(4 << 30, 8)
+    key = 92
+    first = wl.quad_z(101, 0.5, (0.5, 2.5))
+    fetch(hj, s, run(hj, s, first, 2, 0.0, hj.HJ_WARM, key, tol=1e-5), first)
+    moved = wl.quad_z(101, 0.6, (0.65, 2.65))
+    rc, st1, W = fetch(hj, s, run(hj, s, moved, 2, 0.0, hj.HJ_WARM, key, tol=1e-5), moved)
+    stats = hj.hj_server_get_stats(s)
+    with pytest.raises(hj.HJError):
+        hj._check(hj.lib().hj_server_set_translated_starts(s, 2))
+    hj.hj_server_destroy(s)
+    assert rc == hj.HJ_OK
+    assert stats["translated_starts"] == 0 and stats["warm_starts"] == 0
+    assert stats["cold_starts"] == 2
+    g = hj.Grid.from_spec(moved)
+    stc = g.solve(hj.HJ_COLD, scheme=2, tol=1e-5)
+    Wc = g.value()
+    g.close()
+    assert st1["steps"] == stc["steps"]
+    assert np.array_equal(W, Wc)
 
 
 def test_two_coarse_levels_and_coarse_scheme(hj):
