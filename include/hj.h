@@ -517,7 +517,7 @@ hj_status hj_set_launch_shape(hj_grid g, int threads, int tile_rows);
 /* The current launch shape (either pointer may be NULL). */
 hj_status hj_get_launch_shape(hj_grid g, int* threads, int* tile_rows);
 
-/* Shape-specialised stage kernels.  For grids of at least 2^20 nodes the
+/* Shape-specialised stage kernels.  For grids of at least 2^19 nodes the
  * library compiles at run time (NVRTC, from the first use per grid shape,
  * scheme and block size) the stage kernels with the grid's axis lengths and
  * strides as constants, and keeps them for the process: the same arithmetic

@@ -68,7 +68,7 @@ cudaError_t launch_stage(const hjd::DevGrid& g, int scheme, int stage, const hjd
 // finished one (outside any stream capture) and says whether the kernels
 // are ready.  jit_launch sets *used when it launched; otherwise the caller
 // launches the precompiled one.
-constexpr long long kJitNodes = 1ll << 20;
+constexpr long long kJitNodes = 1ll << 19;
 bool jit_wanted(const hjd::DevGrid& g);
 bool jit_prepare(const hjd::DevGrid& g, int scheme, int threads);
 cudaError_t jit_launch(const hjd::DevGrid& g, int scheme, int stage, const hjd::StageArgs& a,

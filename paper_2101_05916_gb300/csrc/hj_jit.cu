@@ -208,13 +208,16 @@ std::string source(const hjd::DevGrid& g, int scheme, int threads, bool local) {
     }
     return s;
   }
-  // 2048 threads per SM: 32 registers per thread, which the folded kernels
-  // fit without spills (40 registers and 1536 threads otherwise)
+  // Resident threads per SM: 2048 (32 registers per thread, which the folded
+  // kernels fit without spills in stages 1-2) for grids of 2^23 nodes and
+  // more, 1536 (40 registers) below.  Measured per WENO5 stage launch: 61^4
+  // and 81^4 run 1-1.3 % faster at 2048, 41^4 1.4 % faster at 1536.
+  const int per_sm = g.npts >= (1 << 23) ? 2048 : 1536;
   for (int st = 1; st <= 3; ++st) {
     std::snprintf(buf, sizeof(buf),
                   "extern \"C\" __global__ void __launch_bounds__(%d, %d)\n"
                   "hj_stage_%d(const hjd::DevGrid g, const hjd::StageArgs a) {\n",
-                  threads, 2048 / threads, st);
+                  threads, std::max(1, per_sm / threads), st);
     s += buf;
     std::snprintf(buf, sizeof(buf), "  hjd::flat_body<%d, %d, %d, %d, %s>(hj_fixed(g), a);\n}\n",
                   g.ndim, scheme, g.model, st, local ? "true" : "false");

@@ -901,7 +901,7 @@ def test_autotune_keeps_value_and_results(hj):
 
 
 def test_shape_specialised_kernels_match_precompiled_bitwise(hj):
-    """Grids of >= 2^20 nodes run stage kernels compiled at run time with the
+    """Grids of >= 2^19 nodes run stage kernels compiled at run time with the
     grid shape as constants: the same values as the precompiled kernels,
     bit for bit, on direct launches and inside captured graphs."""
     cases = [(wl.quad_x4(33, 0.5), 5), (wl.quad_z(1025, 0.5), 2)]
@@ -983,7 +983,7 @@ def test_row_tiles_reject_shapes_that_do_not_fit(hj):
 
 
 def test_specialised_row_tiles_match_flat_bitwise(hj):
-    """Row tiles compiled at run time for a grid of >= 2^20 nodes, on direct
+    """Row tiles compiled at run time for a grid of >= 2^19 nodes, on direct
     launches and inside captured graphs: the same values as the precompiled
     flat kernels, bit for bit."""
     spec = wl.quad_x4(33, 0.5)
