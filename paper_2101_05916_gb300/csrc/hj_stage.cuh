@@ -182,9 +182,11 @@ __host__ __device__ constexpr int tile_row_pitch(int n) {
 //   1. The run is staged in shared memory with 16-byte loads over its
 //      16-byte-aligned cover (fields start 16-byte aligned and carry guard
 //      floats, so the cover never leaves the allocation), each line padded
-//      by R ghost values on both sides: the linear continuation of the line
-//      through its two outermost nodes, the same values load_fast_line
-//      synthesises node by node.
+//      by R values on both sides: the linear continuation of the line
+//      through its two outermost nodes.  The differences that reach into
+//      the padding are replaced by the end rule (edge_diffs), as in the
+//      flat mapping, so the padding only keeps every shared-memory read
+//      defined.
 //   2. Thread t < (lines in the tile) * n then computes node t of the run;
 //      its fastest-axis stencil reads the staged line, the other axes read
 //      global memory as in the flat mapping.
