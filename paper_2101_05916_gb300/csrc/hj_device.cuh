@@ -411,7 +411,9 @@ __device__ __forceinline__ void weno5_pair(float D0, float D1, float D2, float D
   const float2 X2 = make_float2(D2, -D3);
   const float2 k = f2s(39.f / 64.f);
   float2 kB2 = mul2(mul2(k, B), B);
-  float2 kC2 = mul2(mul2(k, C), C);
+  // C holds one value in both lanes: its square term is one scalar product
+  const float kc = (39.f / 64.f) * c * c;
+  const float2 kC2 = make_float2(kc, kc);
   float2 q1 = fma2(f2s(-1.375f), B, A);
   float2 q2 = fma2(f2s(-0.625f), C, B);
   float2 q3 = fma2(f2s(-1.375f), C, E);
