@@ -67,12 +67,12 @@ FLOPS_PER_UPDATE = {("quad_x4", 5): 1624.0}
 BYTES_PER_UPDATE = 32.0
 # DRAM bytes (read + write) per stage launch, averaged over stages 1-3, from
 # one ncu capture of the stage kernels on the 81^4 grid (three consecutive
-# launches of each of two steps, --clock-control none): 307.0, 493.6 and
-# 483.6 MB.  Reset to None whenever the stage kernel changes.
-STAGE_TRAFFIC_BYTES_81 = 428126336.0
+# launches of each of two steps, --clock-control none): 307.3, 493.8 and
+# 482.8 MB.  Reset to None whenever the stage kernel changes.
+STAGE_TRAFFIC_BYTES_81 = 427972352.0
 # The same for the 41^4 grid (11.3, 22.6 and 22.6 MB, reads only: the
 # 45 MB working set stays in L2 and the writes never reach DRAM).
-STAGE_TRAFFIC_BYTES_41 = 18851669.0
+STAGE_TRAFFIC_BYTES_41 = 18853803.0
 FP32_LANES_PER_SM = 128
 
 
