@@ -21,7 +21,8 @@ Other keys:
   latency_ms   p50/p99 of the update against the plain cold 81^4 solve, with
                the node-by-node accuracy check of the update against it.
   roofline     the dominant kernel (the WENO5 stage kernel on the 81^4 grid):
-               per-launch device time from a differenced fixed-step pass.
+               per-launch device time, the median of repeated fixed-step
+               passes timed with CUDA events.
   secondary    the 41^4 cold solve + warm update pair (the 4-D configuration
                with cold vs warm start), with its own rate and roofline.
   scenarios    the decomposed batched update, coarse-to-fine variants, local
@@ -235,27 +236,26 @@ def fp32_peak_tflops(peaks):
     return sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, sms, mhz
 
 
-def stage_launch_seconds(hj, g, stream, k_short=4, k_long=12, reps=2):
-    """Average device time of one stage launch on grid g: two fixed-step
-    passes of k_short and k_long TVD-RK3 steps, CUDA events on the grid's
-    stream, differenced so that the init kernel and the solve's set-up
-    cancel; the best of `reps`."""
+def stage_launch_seconds(hj, g, stream, steps=12, reps=5):
+    """Average device time of one stage launch on grid g: `reps` warm
+    passes of `steps` TVD-RK3 steps, each timed alone with CUDA events on
+    the grid's stream; the median pass over its 3 * steps stage launches.
+    The pass's initialisation kernel and set-up count against the launches,
+    so the figure errs high (by about 0.2 % at 81^4).  Differencing a short
+    and a long pass read 1-2 % low on GB300: the two passes do not carry
+    the same fixed cost."""
     import torch
-    best = None
+    per = []
     for _ in range(reps):
-        ts = []
-        for k in (k_short, k_long):
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            g.solve(hj.HJ_WARM, scheme=5, fixed_steps=k, clamp=CLAMP)
-            e1.record(stream)
-            e1.synchronize()
-            ts.append(e0.elapsed_time(e1) / 1e3)
-        v = (ts[1] - ts[0]) / (3 * (k_long - k_short))
-        best = v if best is None else min(best, v)
-    return best
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.solve(hj.HJ_WARM, scheme=5, fixed_steps=steps, clamp=CLAMP)
+        e1.record(stream)
+        e1.synchronize()
+        per.append(e0.elapsed_time(e1) / 1e3 / (3 * steps))
+    return statistics.median(per)
 
 
 def roofline_entry(hj, npts, per_launch_s, peak, sms, mhz, traffic, kernel, peaks):
