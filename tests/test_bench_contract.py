@@ -22,6 +22,11 @@ def test_reference_arm_line():
     assert line["config"]["workload"] == "x4_adaptive_31^4->81^4_weno5_update"
     assert line["config"]["grid_fine"] == [81, 81, 81, 81]
     assert line["config"]["grid_coarse"] == [31, 31, 31, 31]
+    # the same config dict as the GB300 arm's line; the sample is described
+    # under cpu_baseline
+    import bench
+    assert line["config"] == json.loads(json.dumps(bench.arm_config()))
+    assert "TVD-RK3 step" in line["cpu_baseline"]["sample"]
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["unit"] == line["unit"]
