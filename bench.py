@@ -236,12 +236,13 @@ def fp32_peak_tflops(peaks):
     return sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, sms, mhz
 
 
-def stage_launch_seconds(hj, g, stream, steps=12, reps=5):
+def stage_launch_seconds(hj, g, stream, steps=40, reps=5):
     """Average device time of one stage launch on grid g: `reps` warm
     passes of `steps` TVD-RK3 steps, each timed alone with CUDA events on
     the grid's stream; the median pass over its 3 * steps stage launches.
     The pass's initialisation kernel and set-up count against the launches,
-    so the figure errs high (by about 0.2 % at 81^4).  Differencing a short
+    so the figure errs high: 12-step passes read 567 us per 81^4 launch,
+    40-step passes 562 us.  Differencing a short
     and a long pass read 1-2 % low on GB300: the two passes do not carry
     the same fixed cost."""
     import torch
