@@ -537,6 +537,18 @@ long long hj_jit_pending(void);
  * when NVRTC is missing or the compile fails (hj_last_error holds the start
  * of NVRTC's log). */
 hj_status hj_jit_check(int ndim, const int* n, int model, int scheme, int threads);
+/* The same compile with ptxas reporting resources, for a box constraint on
+ * the axes whose bits are set in con_axes (bit d: axis d; the others
+ * unconstrained, as with +-INFINITY in hj_set_constraint): *max_registers
+ * gets the largest register count per thread and *max_spill_bytes the
+ * largest spill-store size (bytes per thread) over the three stage
+ * kernels.  Grids of 2^23 nodes or more are compiled for 2048 resident
+ * threads per SM (at most 32 registers), smaller ones for 1536.  Needs no
+ * device.  HJ_ERR_ARG on bad arguments, NULL outputs or a con_axes that
+ * names no axis of the grid (or one beyond it); HJ_ERR_CUDA when NVRTC is
+ * missing, the compile fails or the log holds no resource report. */
+hj_status hj_jit_check_resources(int ndim, const int* n, int model, int scheme, int threads,
+                                 unsigned con_axes, int* max_registers, int* max_spill_bytes);
 /* The same for the row-tile stage kernels of tile_rows lines per block. */
 hj_status hj_jit_check_tiles(int ndim, const int* n, int model, int scheme, int tile_rows);
 /* The same for the group kernels of a batch of ngrids grids (grid k:

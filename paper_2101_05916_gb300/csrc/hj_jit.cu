@@ -283,7 +283,9 @@ std::string group_source(const std::vector<hjd::DevGrid>& grids, const std::vect
 
 // NVRTC compile of one kernel set (no CUDA calls).  *log, when given,
 // receives NVRTC's log.
-std::vector<char> compile(const std::string& src, std::string* log = nullptr) {
+// verbose: ptxas reports each kernel's registers and spills into the log.
+std::vector<char> compile(const std::string& src, std::string* log = nullptr,
+                          bool verbose = false) {
   std::vector<char> cubin;
   const Nvrtc& n = nvrtc();
   if (!n.ok) return cubin;
@@ -292,9 +294,10 @@ std::vector<char> compile(const std::string& src, std::string* log = nullptr) {
   if (n.create(&prog, src.c_str(), "hj_stage_jit.cu", nh, kJitHeaders, kJitHeaderNames) !=
       NVRTC_SUCCESS)
     return cubin;
-  const char* opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-ftz=true", "-lineinfo"};
+  const char* opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-ftz=true", "-lineinfo",
+                        "--ptxas-options=-v"};
   size_t sz = 0;
-  nvrtcResult rc = n.compile(prog, 4, opts);
+  nvrtcResult rc = n.compile(prog, verbose ? 5 : 4, opts);
   if (log) {
     size_t ls = 0;
     if (n.log_size(prog, &ls) == NVRTC_SUCCESS && ls > 1) {
@@ -515,10 +518,41 @@ void jit_enable(int on) { g_enabled.store(on ? 1 : 0); }
 }  // namespace hjk
 
 static hj_status jit_check(int ndim, const int* n, int model, int scheme, int threads,
-                           int tile_rows);
+                           int tile_rows, int* max_registers = nullptr,
+                           int* max_spill_bytes = nullptr, unsigned con_axes = ~0u);
 
 extern "C" hj_status hj_jit_check(int ndim, const int* n, int model, int scheme, int threads) {
   return jit_check(ndim, n, model, scheme, threads, 0);
+}
+
+extern "C" hj_status hj_jit_check_resources(int ndim, const int* n, int model, int scheme,
+                                            int threads, unsigned con_axes, int* max_registers,
+                                            int* max_spill_bytes) {
+  if (!max_registers || !max_spill_bytes) return hja::fail(HJ_ERR_ARG, "NULL output");
+  if (ndim < 1 || ndim > HJ_MAX_DIM || con_axes == 0u || (con_axes >> ndim) != 0u)
+    return hja::fail(HJ_ERR_ARG, "con_axes must name at least one of the grid's axes");
+  return jit_check(ndim, n, model, scheme, threads, 0, max_registers, max_spill_bytes, con_axes);
+}
+
+// The largest register count and spill-store size over the kernels of a
+// ptxas -v log ("Used N registers", "N bytes spill stores").
+static void parse_resources(const std::string& log, int* regs, int* spill) {
+  *regs = -1;
+  *spill = 0;
+  size_t pos = 0;
+  while ((pos = log.find("Used ", pos)) != std::string::npos) {
+    int v = 0;
+    if (std::sscanf(log.c_str() + pos, "Used %d registers", &v) == 1) *regs = std::max(*regs, v);
+    pos += 5;
+  }
+  pos = 0;
+  const std::string key = " bytes spill stores";
+  while ((pos = log.find(key, pos)) != std::string::npos) {
+    size_t b = pos;
+    while (b > 0 && log[b - 1] >= '0' && log[b - 1] <= '9') --b;
+    if (b < pos) *spill = std::max(*spill, std::atoi(log.c_str() + b));
+    pos += key.size();
+  }
 }
 
 extern "C" hj_status hj_jit_check_tiles(int ndim, const int* n, int model, int scheme,
@@ -528,7 +562,8 @@ extern "C" hj_status hj_jit_check_tiles(int ndim, const int* n, int model, int s
 }
 
 static hj_status jit_check(int ndim, const int* n, int model, int scheme, int threads,
-                           int tile_rows) {
+                           int tile_rows, int* max_registers, int* max_spill_bytes,
+                           unsigned con_axes) {
   if (ndim < 1 || ndim > HJ_MAX_DIM || !n) return hja::fail(HJ_ERR_ARG, "bad grid shape");
   if (model != HJ_DRIFT && model != HJ_QUAD_Z && model != HJ_QUAD_X4)
     return hja::fail(HJ_ERR_ARG, "unknown model %d", model);
@@ -547,8 +582,9 @@ static hj_status jit_check(int ndim, const int* n, int model, int scheme, int th
     g.lo[i] = 0.0;
     g.hi[i] = 1.0;
     g.h[i] = 1.0 / (double)(n[i] - 1);
-    g.ca[i] = 0.25;
-    g.cb[i] = 0.75;
+    const bool con = (con_axes >> i) & 1u;
+    g.ca[i] = con ? 0.25 : -INFINITY;
+    g.cb[i] = con ? 0.75 : INFINITY;
     npts *= n[i];
   }
   if (npts >= (1ll << 31)) return hja::fail(HJ_ERR_ARG, "grid too large");
@@ -562,8 +598,13 @@ static hj_status jit_check(int ndim, const int* n, int model, int scheme, int th
     return hja::fail(HJ_ERR_ARG, "row tile does not fit the grid");
   if (!hjk::nvrtc().ok) return hja::fail(HJ_ERR_CUDA, "NVRTC could not be loaded");
   std::string log;
-  std::vector<char> cubin = hjk::compile(hjk::source(d, scheme, threads, false), &log);
+  const bool verbose = max_registers != nullptr;
+  std::vector<char> cubin = hjk::compile(hjk::source(d, scheme, threads, false), &log, verbose);
   if (cubin.empty()) return hja::fail(HJ_ERR_CUDA, "NVRTC: %.400s", log.c_str());
+  if (verbose) {
+    parse_resources(log, max_registers, max_spill_bytes);
+    if (*max_registers < 0) return hja::fail(HJ_ERR_CUDA, "no ptxas resource report in the log");
+  }
   return HJ_OK;
 }
 

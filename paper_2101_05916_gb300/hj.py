@@ -106,6 +106,7 @@ SIGNATURES = {
     "hj_jit_pending": (_ll, []),
     "hj_jit_check": (_i, [_i, _P(_i), _i, _i, _i]),
     "hj_jit_check_tiles": (_i, [_i, _P(_i), _i, _i, _i]),
+    "hj_jit_check_resources": (_i, [_i, _P(_i), _i, _i, _i, ctypes.c_uint, _P(_i), _P(_i)]),
     "hj_jit_check_group": (_i, [_i, _P(_i), _P(_i), _P(_i), _P(_i)]),
     "hj_set_launch_shape": (_i, [_vp, _i, _i]),
     "hj_set_allocator": (_i, [_vp, _vp, _vp]),
@@ -421,6 +422,22 @@ def hj_jit_check(n: Sequence[int], model, scheme: int, threads: int = 256) -> No
     m = MODELS[model] if isinstance(model, str) else int(model)
     arr = (_i * len(n))(*[int(v) for v in n])
     _check(lib().hj_jit_check(len(n), arr, m, int(scheme), int(threads)))
+
+
+def hj_jit_check_resources(n: Sequence[int], model, scheme: int, threads: int = 256,
+                           con_axes: Sequence[int] = (0,)):
+    """(registers per thread, spill-store bytes per thread), the largest over
+    the three shape-specialised stage kernels, from ptxas through NVRTC (no
+    device needed), with a box constraint on the axes con_axes."""
+    m = MODELS[model] if isinstance(model, str) else int(model)
+    arr = (_i * len(n))(*[int(v) for v in n])
+    mask = 0
+    for a in con_axes:
+        mask |= 1 << int(a)
+    regs, spill = _i(), _i()
+    _check(lib().hj_jit_check_resources(len(n), arr, m, int(scheme), int(threads), mask,
+                                        ctypes.byref(regs), ctypes.byref(spill)))
+    return regs.value, spill.value
 
 
 def hj_jit_check_tiles(n: Sequence[int], model, scheme: int, tile_rows: int) -> None:

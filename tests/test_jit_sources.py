@@ -27,6 +27,24 @@ def test_bad_arguments_are_rejected():
         hj.hj_jit_check([2, 41], "quad_z", 2, 256)
 
 
+def test_large_grid_stage_kernels_fit_2048_threads_per_sm_without_spills():
+    """The WENO5 stage kernels of the x-subsystem (box on the position axis)
+    compiled for 81^4 and 61^4 grids run 2048 resident threads per SM: 32
+    registers per thread, nothing spilled.  41^4 keeps 1536 threads (40
+    registers), also without spills."""
+    for n in (81, 61):
+        for threads in (128, 256, 512):
+            regs, spill = hj.hj_jit_check_resources([n] * 4, "quad_x4", 5, threads)
+            assert regs <= 32 and spill == 0, (n, threads, regs, spill)
+    regs, spill = hj.hj_jit_check_resources([41] * 4, "quad_x4", 5, 256)
+    assert 32 < regs <= 40 and spill == 0, (regs, spill)
+    regs, spill = hj.hj_jit_check_resources([1025, 1025], "quad_z", 2, 256, con_axes=(0, 1))
+    assert regs <= 40 and spill == 0
+    for bad in ((), (4,)):
+        with pytest.raises(hj.HJError):
+            hj.hj_jit_check_resources([81] * 4, "quad_x4", 5, 256, con_axes=bad)
+
+
 TILE_CASES = ([("quad_x4", [41, 41, 41, 41], s, r) for s in (1, 2, 5) for r in (3, 6, 7)]
               + [("quad_x4", [81, 81, 81, 81], 5, r) for r in (3, 5, 12)]
               + [("quad_z", [201, 201], s, r) for s in (2, 5) for r in (1, 2, 5)]
