@@ -285,7 +285,7 @@ __device__ __forceinline__ double node_diff2(const DevGrid& g, const float* W, i
 // replaced.  Selects, not branches: lanes away from the ends keep every
 // slot.  n >= 2 keeps the two replaced ranges apart.
 template <int R>
-__device__ __forceinline__ void edge_diffs(float (&Dk)[2 * R], int i, int n) {
+__host__ __device__ __forceinline__ void edge_diffs(float (&Dk)[2 * R], int i, int n) {
   const int r = n - 1 - i;
   float dl = Dk[R], dr = Dk[R - 1];
 #pragma unroll
@@ -300,7 +300,7 @@ __device__ __forceinline__ void edge_diffs(float (&Dk)[2 * R], int i, int n) {
 }
 
 template <int R>
-__device__ __forceinline__ void diffs_of(const float (&v)[2 * R + 1], float (&Dk)[2 * R]) {
+__host__ __device__ __forceinline__ void diffs_of(const float (&v)[2 * R + 1], float (&Dk)[2 * R]) {
 #pragma unroll
   for (int k = 0; k < 2 * R; ++k) Dk[k] = v[k + 1] - v[k];
 }
